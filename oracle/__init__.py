@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for the near-field direct sum (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this package. The product library never imports it, and it
+imports nothing from the product: the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, OpenMP over
+sinks). This module compiles it with gcc into ``oracle/_build/liboracle.so``
+and marshals numpy arrays through ctypes. Each function cites the passage of
+Maksimova et al. 2021 ("AbacusSummit", arXiv 2110.11398) that it follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_OK, ORC_EINVAL, ORC_ERANGE, ORC_ENOMEM = 0, -1, -2, -3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc (-O2, OpenMP, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
+               "-shared", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+            lib.orc_bin.argtypes = [i64, vp, dbl, i32, vp, vp, vp, vp]
+            lib.orc_bin.restype = i32
+            lib.orc_accel.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, i64, vp]
+            lib.orc_accel.restype = i32
+            lib.orc_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, vp, i64, vp]
+            lib.orc_vjp.restype = i32
+            lib.orc_interactions.argtypes = [i64, vp, i32, i32, vp]
+            lib.orc_interactions.restype = i64
+            lib.orc_num_threads.argtypes = []
+            lib.orc_num_threads.restype = i32
+            lib.orc_set_num_threads.argtypes = [i32]
+            lib.orc_set_num_threads.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(rc: int, what: str):
+    if rc != ORC_OK:
+        raise OracleError(f"{what} failed with code {rc}")
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    _load().orc_set_num_threads(int(t))
+
+
+def bin_particles(pos32: np.ndarray, L: float, cpd: int):
+    """Cell binning and stable counting sort (Sec. 3.1, cubic lattice of cells).
+
+    Returns dict with ``cid`` (int32 linear cell id, x slowest), ``cell_start``
+    (int64, CPD^3+1), ``perm`` (int64; sorted slot -> input index, stable) and
+    ``rel`` (float32 (N,3) cell-relative coordinates in cell units, sorted).
+    """
+    pos32 = np.ascontiguousarray(pos32, dtype=np.float32)
+    n = pos32.shape[0]
+    ncell = cpd ** 3
+    cid = np.empty(n, np.int32)
+    cs = np.empty(ncell + 1, np.int64)
+    perm = np.empty(n, np.int64)
+    rel = np.empty((n, 3), np.float32)
+    _check(_load().orc_bin(n, _ptr(pos32), float(L), int(cpd), _ptr(cid), _ptr(cs),
+                           _ptr(perm), _ptr(rel)), "orc_bin")
+    return {"cid": cid, "cell_start": cs, "perm": perm, "rel": rel}
+
+
+def _prep(pos, cid, mass, sinks):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cid = np.ascontiguousarray(cid, dtype=np.int32)
+    mass = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+    sinks = None if sinks is None else np.ascontiguousarray(sinks, dtype=np.int64)
+    return pos, cid, mass, sinks
+
+
+def accel(pos, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float = 1.0,
+          sinks=None, cid=None) -> np.ndarray:
+    """Near-field Plummer-softened accelerations in FP64 (Sec. 3.1; Sec. 5.2).
+
+    ``pos`` may be float32 or float64 (N,3). If ``cid`` is None the cells come
+    from :func:`bin_particles` on float32 positions; pass ``cid`` to hold the
+    binning fixed. Returns (len(sinks) or N, 3) float64.
+    """
+    if cid is None:
+        cid = bin_particles(np.asarray(pos, np.float32), L, cpd)["cid"]
+    pos, cid, mass, sinks = _prep(pos, cid, mass, sinks)
+    n = pos.shape[0]
+    ns = n if sinks is None else sinks.shape[0]
+    out = np.empty((ns, 3), np.float64)
+    _check(_load().orc_accel(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L),
+                             int(cpd), int(R), float(eps), _ptr(sinks), ns, _ptr(out)),
+           "orc_accel")
+    return out
+
+
+def vjp(pos, w, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float = 1.0,
+        sinks=None, cid=None) -> np.ndarray:
+    """Vector-Jacobian product d(sum_i w_i . a_i)/dx with the binning held fixed.
+
+    g_k = sum_j J(Delta_kj)(m_k w_j - m_j w_k), J = s^-3/2 I - 3 s^-5/2 D D^T
+    (derivative of the Plummer near-field sum of Sec. 3.1 / Sec. 5.2).
+    """
+    if cid is None:
+        cid = bin_particles(np.asarray(pos, np.float32), L, cpd)["cid"]
+    pos, cid, mass, sinks = _prep(pos, cid, mass, sinks)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = pos.shape[0]
+    ns = n if sinks is None else sinks.shape[0]
+    out = np.empty((ns, 3), np.float64)
+    _check(_load().orc_vjp(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L),
+                           int(cpd), int(R), float(eps), _ptr(w), _ptr(sinks), ns, _ptr(out)),
+           "orc_vjp")
+    return out
+
+
+def interactions(cid, cpd: int, R: int, per_sink: bool = False):
+    """Pairwise interaction count of the near-field sum ("directs", Sec. 4.3).
+
+    sum_c n_c * sum_{|d|<=R} n_{c+d}, self pairs included. With ``per_sink``
+    also returns the number of sources seen by each particle.
+    """
+    cid = np.ascontiguousarray(cid, dtype=np.int32)
+    n = cid.shape[0]
+    nsrc = np.empty(n, np.int64) if per_sink else None
+    tot = int(_load().orc_interactions(n, _ptr(cid), int(cpd), int(R), _ptr(nsrc)))
+    if tot < 0:
+        raise OracleError("orc_interactions: out of memory")
+    return (tot, nsrc) if per_sink else tot
