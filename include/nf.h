@@ -1,0 +1,222 @@
+/*
+ * nf.h -- C ABI of libnf, the GB300 (sm_103a) near-field direct-sum library.
+ *
+ * The operation (Maksimova et al. 2021, "AbacusSummit", Sec. 3.1): a periodic
+ * box of side L is cut into CPD^3 cubic cells; the near-field acceleration of
+ * a particle is the direct sum over every particle of the cells whose offset
+ * d from its own cell lies in [-R, R]^3 (R = near-field radius in cells, 2 in
+ * the paper), each source cell taken at the one periodic image that sits at
+ * offset d. The pair law is Plummer softening, the gradient of the potential
+ * -G m / sqrt(r^2 + eps^2) named in Sec. 5.2:
+ *
+ *     a_i = sum_j G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2)
+ *
+ * G is folded into the masses. The self pair (j = i) is included and is 0.
+ *
+ * Conventions for every entry point:
+ *   - All array pointers are DEVICE pointers owned by the caller, except
+ *     where a parameter says "host". Arrays are C-contiguous; a position or
+ *     acceleration array is N x 3 float32, particle-major (x, y, z per row),
+ *     in the caller's (input) particle order.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream). Calls return once the work is enqueued,
+ *     except where a function says it synchronises.
+ *   - The library owns its internal buffers (cell-sorted particles, cell
+ *     table, work list). It keeps no pointer to caller memory after a call
+ *     returns: nf_bin_particles copies positions into cell-sorted storage, so
+ *     compute calls use that snapshot.
+ *   - Errors are returned as negative nf_status codes; no C++ exception
+ *     crosses the ABI and no kernel traps. nf_last_error() gives the message.
+ *   - One context is bound to one device and is not thread-safe: calls on
+ *     the same context must be serialised by the caller.
+ */
+#ifndef NF_H
+#define NF_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NF_API __attribute__((visibility("default")))
+#else
+#define NF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nf_ctx nf_ctx;
+
+typedef enum nf_status {
+    NF_OK = 0,
+    NF_EINVAL = -1,    /* bad argument (sizes, CPD < 2R+1, eps <= 0, N > capacity, ...) */
+    NF_ERANGE = -2,    /* a position component is not finite or outside [0, L) */
+    NF_ENOMEM = -3,    /* device or host allocation failed */
+    NF_ECUDA = -4,     /* a CUDA runtime call failed; see nf_last_error */
+    NF_ESTATE = -5,    /* call out of order (e.g. compute before binning) */
+    NF_ETIMEOUT = -6   /* reserved: no kernel in this library spin-waits */
+} nf_status;
+
+typedef enum nf_softening {
+    NF_SOFT_PLUMMER = 0     /* Plummer law above (Sec. 5.2) */
+} nf_softening;
+
+typedef enum nf_precision {
+    NF_PREC_FP32 = 0,       /* FP32 pair arithmetic on cell-relative coordinates */
+    NF_PREC_FP32_COMP = 1,  /* same, per-sink sums kept as compensated (TwoSum) pairs */
+    NF_PREC_FP64_REF = 2    /* FP64 pair arithmetic on the GPU (reference timing) */
+} nf_precision;
+
+/* Figures of the last binning / compute on a context (see nf_get_stats). */
+typedef struct nf_stats {
+    int64_t n_particles;     /* particles binned by the last nf_bin_particles */
+    int64_t n_cells;         /* total cells over all boxes */
+    int64_t interactions;    /* pairwise interactions of one force pass, self
+                                pairs included: sum_c n_c * sum_{|d|<=R} n_{c+d} */
+    int64_t max_occupancy;   /* largest cell population */
+    int64_t n_items;         /* work items of the last compute */
+    double  momentum[3];     /* sum_i m_i a_i of the last nf_compute_accel, FP64 */
+    double  abs_momentum;    /* sum_i m_i |a_i| (scale for momentum[]) */
+    double  bin_ms;          /* device time of the last binning (CUDA events) */
+    double  pair_ms;         /* device time of the last pair (or adjoint) kernel */
+    int64_t kernel_launches; /* kernels launched by this context so far, graph
+                                replays counted kernel by kernel */
+} nf_stats;
+
+/* Launch shape of the pair kernels. sinks_per_lane in {1,2,4}; warps_per_block
+ * in {2,4,8,16}; blocks_per_sm = 0 picks the occupancy maximum; use_graph = 1
+ * replays the compute phase from a captured CUDA graph. */
+typedef struct nf_tuning {
+    int sinks_per_lane;
+    int warps_per_block;
+    int blocks_per_sm;
+    int use_graph;
+} nf_tuning;
+
+/*
+ * nf_init -- create a context for n_boxes independent periodic boxes.
+ *   out        host: receives the context (set to NULL on failure)
+ *   device     CUDA device ordinal
+ *   n_boxes    >= 1
+ *   box_size   host [n_boxes]: L of each box (> 0)
+ *   cpd        host [n_boxes]: cells per dimension of each box, 2R+1 <= CPD <= 1024
+ *   radius     near-field radius R in cells, 1..3 (the paper uses 2; Sec. 3.1)
+ *   eps        host [n_boxes]: Plummer softening length of each box (> 0)
+ *   softening  NF_SOFT_PLUMMER
+ *   precision  an nf_precision value
+ *   capacity   largest total particle count that will be binned (< 2^31)
+ * Allocates all device buffers for `capacity` particles up front.
+ * Returns NF_OK, NF_EINVAL, NF_ENOMEM or NF_ECUDA.
+ */
+NF_API int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const int *cpd,
+            int radius, const double *eps, int softening, int precision, int64_t capacity);
+
+/*
+ * nf_bin_particles -- assign particles to cells and sort them by cell
+ * (the cell lattice of Sec. 3.1): cell id, per-cell count, exclusive prefix
+ * scan, stable scatter into cell order with cell-relative FP32 coordinates.
+ *   pos          device [N x 3] float32, every component in [0, L) of its box
+ *   mass         device [N] float32 G*m per particle, or NULL for equal masses
+ *   mass_if_null G*m used for every particle when mass == NULL
+ *   n            total particles N (0 <= N <= capacity)
+ *   box_offsets  host [n_boxes+1]: particles of box b are rows
+ *                [box_offsets[b], box_offsets[b+1]); NULL when n_boxes == 1
+ *   stream       cudaStream_t
+ * Synchronises `stream` once at the end to report NF_ERANGE for an invalid
+ * position (such particles are binned to a safe cell and the context is
+ * marked unbinned). Returns NF_OK, NF_EINVAL, NF_ERANGE, NF_ESTATE or NF_ECUDA.
+ */
+NF_API int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double mass_if_null,
+                     int64_t n, const int64_t *box_offsets, void *stream);
+
+/*
+ * nf_compute_accel -- near-field accelerations of every binned particle
+ * (the direct O(N^2) near-field sum of Sec. 3.1 over (2R+1)^3 cells).
+ *   acc     device [N x 3] float32 out, input particle order, caller-owned
+ * Also accumulates the FP64 momentum diagnostic sum_i m_i a_i (nf_get_stats).
+ * Returns NF_OK, NF_EINVAL, NF_ESTATE (not binned) or NF_ECUDA. Asynchronous.
+ */
+NF_API int nf_compute_accel(nf_ctx *ctx, float *acc, void *stream);
+
+/*
+ * nf_compute_accel_f64 -- as nf_compute_accel, with the accelerations written
+ * as float64 (the natural output of NF_PREC_FP64_REF; the other precisions
+ * widen their FP32 sums).
+ *   acc     device [N x 3] float64 out, input particle order
+ */
+NF_API int nf_compute_accel_f64(nf_ctx *ctx, double *acc, void *stream);
+
+/*
+ * nf_compute_accel_vjp -- vector-Jacobian product of the accelerations with
+ * respect to the positions, for the scalar sum_i w_i . a_i with the binning of
+ * the last nf_bin_particles held fixed:
+ *     g_k = sum_{j near k} J(D_kj) (m_k w_j - m_j w_k),
+ *     J(D) = s^(-3/2) I - 3 s^(-5/2) D D^T,  s = |D|^2 + eps^2,  D_kj = x_j - x_k.
+ * Pair terms are recomputed, not stored.
+ *   w         device [N x 3] float32 cotangent, input order
+ *   grad_pos  device [N x 3] float32 out, input order, caller-owned
+ * Returns NF_OK, NF_ESTATE or NF_ECUDA. Asynchronous. FP32 (and FP32_COMP
+ * contexts) use FP32 arithmetic; NF_PREC_FP64_REF contexts use FP64.
+ */
+NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream);
+
+/*
+ * nf_accel_host -- end-to-end convenience call on HOST buffers: copies
+ * positions (and masses) to the device, bins, computes the accelerations and
+ * copies them back, then synchronises `stream`.
+ *   pos_host   host [N x 3] float32 (pinned memory gives full copy speed)
+ *   mass_host  host [N] float32 or NULL (then mass_if_null)
+ *   acc_host   host [N x 3] float32 out
+ * Device staging buffers are allocated on first use and kept by the context.
+ */
+NF_API int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, double mass_if_null,
+                  int64_t n, const int64_t *box_offsets, float *acc_host, void *stream);
+
+/*
+ * nf_copy_binning -- copy the result of the last nf_bin_particles (the cell
+ * lattice and cell order of Sec. 3.1) into caller buffers, for inspection and
+ * testing. Any pointer may be NULL.
+ *   cell_start  device [n_cells + 1] int32: first sorted slot of each cell;
+ *               box b's cells start at sum_{b' < b} CPD_b'^3, and within a box
+ *               the cell id is (cx * CPD + cy) * CPD + cz
+ *   perm        device [N] int32: input index of each sorted slot (stable:
+ *               particles of one cell keep their input order)
+ *   sorted      device [N x 4] float32: per sorted slot (rx, ry, rz, G m) with
+ *               r = float32(u - (c + 0.5)), u = (x * CPD) / L in double, in
+ *               cell units
+ * Asynchronous on `stream`. Returns NF_OK, NF_EINVAL, NF_ESTATE or NF_ECUDA.
+ */
+NF_API int nf_copy_binning(nf_ctx *ctx, int32_t *cell_start, int32_t *perm, float *sorted,
+                           void *stream);
+
+/* nf_get_stats -- copy the figures of the last calls into *out (host).
+ * Synchronises the stream of the last compute call. */
+NF_API int nf_get_stats(nf_ctx *ctx, nf_stats *out);
+
+/* nf_set_tuning / nf_get_tuning -- read or replace the launch shape. */
+NF_API int nf_set_tuning(nf_ctx *ctx, const nf_tuning *t);
+NF_API int nf_get_tuning(const nf_ctx *ctx, nf_tuning *t);
+
+/*
+ * nf_autotune -- time every candidate launch shape of the pair kernel on the
+ * currently binned particles (CUDA events on `stream`, `reps` launches each),
+ * keep the fastest in the context and copy it to *best (may be NULL).
+ * Synchronises `stream`. Requires a prior nf_bin_particles.
+ */
+NF_API int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream);
+
+/* nf_last_error -- message of the last failing call on ctx (never NULL);
+ * with ctx == NULL, the message of the last failing nf_init in this thread. */
+NF_API const char *nf_last_error(const nf_ctx *ctx);
+
+/* nf_status_string -- static name of a status code. */
+NF_API const char *nf_status_string(int status);
+
+/* nf_free -- release the context and all its device memory; NULL is a no-op. */
+NF_API void nf_free(nf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NF_H */

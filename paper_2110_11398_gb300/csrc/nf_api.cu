@@ -1,0 +1,566 @@
+// nf_api.cu -- the C ABI of libnf (declared in include/nf.h): context
+// lifetime, argument checks, CUDA-graph replay of the compute phase, the
+// launch-shape autotuner, statistics and the host-buffer end-to-end call.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nf.h"
+#include "nf_ctx.h"
+#include "nf_internal.cuh"
+
+using nf::Ctx;
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(Ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_init_err = msg;
+    return code;
+}
+
+int cuda_fail(Ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                    cudaGetErrorString(e) + ")";
+    return fail(c, NF_ECUDA, m);
+}
+
+#define NF_CK(ctx, call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)count);
+}
+
+bool is_pow2(double L) {
+    int ex;
+    const double m = std::frexp(L, &ex);
+    return m == 0.5;
+}
+
+void release(Ctx *c) {
+    if (!c) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    void *bufs[] = {c->boxes_d, c->poff_d, c->keys_a, c->keys_b, c->vals_a, c->vals_b,
+                    c->count, c->cell_start, c->scan_tmp, c->radix_hist, c->sorted,
+                    c->sorted_d, c->w_sorted, c->nsrc_cell, c->items, c->decomp_d,
+                    c->state, c->mom_partial, c->mom_result, c->st_pos, c->st_mass, c->st_acc};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->state_h) cudaFreeHost(c->state_h);
+    if (c->mom_h) cudaFreeHost(c->mom_h);
+    if (c->g_fwd.exec) cudaGraphExecDestroy(c->g_fwd.exec);
+    if (c->g_vjp.exec) cudaGraphExecDestroy(c->g_vjp.exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaEvent_t evs[] = {c->ev_bin0, c->ev_bin1, c->ev_pair0, c->ev_pair1};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete c;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool valid_tuning(const nf_tuning &t) {
+    const int k = t.sinks_per_lane, w = t.warps_per_block;
+    return (k == 1 || k == 2 || k == 4) && (w == 2 || w == 4 || w == 8 || w == 16) &&
+           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32;
+}
+
+int ensure_decomp(Ctx *c, int K, cudaStream_t s) {
+    if (c->decomp_k == K) return NF_OK;
+    nf::Decomp h;
+    nf::make_decomp(K, &h);
+    // the table is read by the work-list kernels; a synchronous copy keeps it
+    // valid for graphs captured afterwards
+    NF_CK(c, cudaStreamSynchronize(s));
+    NF_CK(c, cudaMemcpy(c->decomp_d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    c->decomp_k = K;
+    return NF_OK;
+}
+
+// The compute phase: work list, pair kernel, momentum diagnostic and the
+// copy of the counters to pinned host memory.
+cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = nf::launch_worklist(c, s))) return e;
+    if ((e = cudaEventRecord(c->ev_pair0, s))) return e;
+    if ((e = nf::launch_pairs(c, acc, f64, c->tune, s))) return e;
+    if ((e = cudaEventRecord(c->ev_pair1, s))) return e;
+    if ((e = nf::launch_momentum(c, acc, f64, s))) return e;
+    if ((e = cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s)))
+        return e;
+    return cudaMemcpyAsync(c->mom_h, c->mom_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t enqueue_vjp(Ctx *c, const float *w, float *grad, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = nf::launch_worklist(c, s))) return e;
+    if ((e = cudaEventRecord(c->ev_pair0, s))) return e;
+    if ((e = nf::launch_vjp(c, w, grad, c->tune, s))) return e;
+    if ((e = cudaEventRecord(c->ev_pair1, s))) return e;
+    return cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s);
+}
+
+// Replay `enqueue` from a CUDA graph captured on the private stream; the
+// graph is re-captured (and updated in place when possible) whenever `key`
+// changes. Captures are thread-local so other threads' work is unaffected.
+template <typename F>
+cudaError_t run_graph(Ctx *c, nf::GraphSlot &slot, const std::vector<uint64_t> &key, F enqueue,
+                      cudaStream_t s) {
+    cudaError_t e;
+    if (!slot.exec || slot.key != key) {
+        if ((e = cudaStreamSynchronize(s))) return e;
+        cudaGraph_t g = nullptr;
+        const int64_t before = c->launches;
+        if ((e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal))) return e;
+        cudaError_t ee = enqueue(c->cap_stream);
+        e = cudaStreamEndCapture(c->cap_stream, &g);
+        slot.n_kernels = c->launches - before;   // captured, not yet run
+        c->launches = before;
+        if (ee) { if (g) cudaGraphDestroy(g); return ee; }
+        if (e) return e;
+        bool updated = false;
+        if (slot.exec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess) updated = true;
+            else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(slot.exec);
+                slot.exec = nullptr;
+            }
+        }
+        if (!updated) {
+            e = cudaGraphInstantiate(&slot.exec, g, 0);
+            if (e) { cudaGraphDestroy(g); slot.exec = nullptr; return e; }
+        }
+        cudaGraphDestroy(g);
+        slot.key = key;
+    }
+    c->launches += slot.n_kernels;
+    return cudaGraphLaunch(slot.exec, s);
+}
+
+int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel: no binned particles (call nf_bin_particles first)");
+    if (!acc && c->n > 0) return fail(c, NF_EINVAL, "nf_compute_accel: acc is NULL");
+    int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
+    if (rc) return rc;
+    cudaError_t e;
+    if (c->tune.use_graph) {
+        std::vector<uint64_t> key = {(uint64_t)(uintptr_t)acc, (uint64_t)f64, (uint64_t)c->n,
+                                     (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
+                                     (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
+                                     (uint64_t)c->equal_mass};
+        e = run_graph(c, c->g_fwd, key, [&](cudaStream_t cs) { return enqueue_forward(c, acc, f64, cs); }, s);
+    } else {
+        e = enqueue_forward(c, acc, f64, s);
+    }
+    if (e) return cuda_fail(c, e, "nf_compute_accel");
+    c->have_momentum = 1;
+    c->have_pair_time = 1;
+    c->last_stream = s;
+    return NF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nf_status_string(int status) {
+    switch (status) {
+        case NF_OK: return "NF_OK";
+        case NF_EINVAL: return "NF_EINVAL";
+        case NF_ERANGE: return "NF_ERANGE";
+        case NF_ENOMEM: return "NF_ENOMEM";
+        case NF_ECUDA: return "NF_ECUDA";
+        case NF_ESTATE: return "NF_ESTATE";
+        case NF_ETIMEOUT: return "NF_ETIMEOUT";
+        default: return "NF_UNKNOWN";
+    }
+}
+
+const char *nf_last_error(const nf_ctx *ctx) {
+    if (!ctx) return g_init_err.c_str();
+    return reinterpret_cast<const Ctx *>(ctx)->err.c_str();
+}
+
+int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const int *cpd,
+            int radius, const double *eps, int softening, int precision, int64_t capacity) {
+    if (!out) return fail(nullptr, NF_EINVAL, "nf_init: out is NULL");
+    *out = nullptr;
+    if (n_boxes < 1 || n_boxes > (1 << 20))
+        return fail(nullptr, NF_EINVAL, "nf_init: n_boxes must be in [1, 2^20]");
+    if (!box_size || !cpd || !eps) return fail(nullptr, NF_EINVAL, "nf_init: box_size, cpd and eps are required");
+    if (radius < 1 || radius > nf::kMaxRadius)
+        return fail(nullptr, NF_EINVAL, "nf_init: radius must be 1, 2 or 3");
+    if (softening != NF_SOFT_PLUMMER) return fail(nullptr, NF_EINVAL, "nf_init: unsupported softening");
+    if (precision < NF_PREC_FP32 || precision > NF_PREC_FP64_REF)
+        return fail(nullptr, NF_EINVAL, "nf_init: unknown precision");
+    if (capacity < 0 || capacity >= ((int64_t)1 << 31) - 1)
+        return fail(nullptr, NF_EINVAL, "nf_init: capacity must be in [0, 2^31 - 1)");
+    int64_t n_cells = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        if (!(box_size[b] > 0.0) || !std::isfinite(box_size[b]))
+            return fail(nullptr, NF_EINVAL, "nf_init: box_size must be finite and > 0");
+        if (cpd[b] < 2 * radius + 1 || cpd[b] > 1024)
+            return fail(nullptr, NF_EINVAL, "nf_init: cpd must satisfy 2R+1 <= cpd <= 1024");
+        if (!(eps[b] > 0.0) || !std::isfinite(eps[b]))
+            return fail(nullptr, NF_EINVAL, "nf_init: eps must be finite and > 0");
+        n_cells += (int64_t)cpd[b] * cpd[b] * cpd[b];
+    }
+    if (n_cells >= ((int64_t)1 << 30))
+        return fail(nullptr, NF_EINVAL, "nf_init: total cells must stay below 2^30");
+    if (nf::scan_tmp_ints(n_cells) > 8192 ||
+        nf::scan_tmp_ints(nf::radix_tiles(capacity) * 256) > 8192)
+        return fail(nullptr, NF_EINVAL, "nf_init: too many cells or particles for the scan");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, NF_ECUDA, "nf_init: no such CUDA device");
+    }
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return fail(nullptr, NF_ENOMEM, "nf_init: out of host memory");
+    DeviceGuard guard(device);
+    c->device = device;
+    c->n_boxes = n_boxes;
+    c->R = radius;
+    c->precision = precision;
+    c->capacity = capacity;
+    c->n_cells = n_cells;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    c->pow2_all = 1;
+    int64_t off = 0;
+    for (int b = 0; b < n_boxes; ++b) {
+        nf::BoxDev B{};
+        const double L = box_size[b], h = L / cpd[b];
+        B.L = L;
+        B.cpd_d = (double)cpd[b];
+        B.cpd = cpd[b];
+        B.cell_off = (int)off;
+        B.eps2_d = (eps[b] / h) * (eps[b] / h);
+        B.inv_h2_d = 1.0 / (h * h);
+        B.inv_h3_d = 1.0 / (h * h * h);
+        B.eps2 = (float)B.eps2_d;
+        B.inv_h2 = (float)B.inv_h2_d;
+        B.inv_h3 = (float)B.inv_h3_d;
+        c->boxes_h.push_back(B);
+        if (!is_pow2(L)) c->pow2_all = 0;
+        off += (int64_t)cpd[b] * cpd[b] * cpd[b];
+    }
+    const int64_t cap = capacity > 0 ? capacity : 1;
+    const int64_t tiles = nf::radix_tiles(cap);
+    c->max_tiles = tiles;
+    cudaError_t e = cudaSuccess;
+#define NF_AL(p, cnt) if (!e) e = dalloc(&(p), (cnt))
+    NF_AL(c->boxes_d, n_boxes);
+    NF_AL(c->poff_d, n_boxes + 1);
+    NF_AL(c->keys_a, cap);
+    NF_AL(c->keys_b, cap);
+    NF_AL(c->vals_a, cap);
+    NF_AL(c->vals_b, cap);
+    NF_AL(c->count, n_cells);
+    NF_AL(c->cell_start, n_cells + 1);
+    const int64_t tmp_ints = std::max(nf::scan_tmp_ints(n_cells), nf::scan_tmp_ints(tiles * 256));
+    NF_AL(c->scan_tmp, tmp_ints);
+    NF_AL(c->radix_hist, tiles * 256 + 1);
+    NF_AL(c->sorted, cap);
+    if (precision == NF_PREC_FP64_REF) NF_AL(c->sorted_d, cap);
+    NF_AL(c->w_sorted, cap);
+    NF_AL(c->nsrc_cell, n_cells);
+    NF_AL(c->items, cap);
+    NF_AL(c->decomp_d, 1);
+    NF_AL(c->state, 1);
+    NF_AL(c->mom_partial, (int64_t)nf::kMomBlocks * 4);
+    NF_AL(c->mom_result, 4);
+#undef NF_AL
+    if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->state_h), sizeof(nf::DevState));
+    if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->mom_h), 4 * sizeof(double));
+    if (!e) e = cudaMemcpy(c->boxes_d, c->boxes_h.data(), sizeof(nf::BoxDev) * n_boxes, cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemset(c->state, 0, sizeof(nf::DevState));
+    if (!e) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreate(&c->ev_bin0);
+    if (!e) e = cudaEventCreate(&c->ev_bin1);
+    if (!e) e = cudaEventCreate(&c->ev_pair0);
+    if (!e) e = cudaEventCreate(&c->ev_pair1);
+    if (e) {
+        const bool oom = e == cudaErrorMemoryAllocation;
+        std::string m = std::string("nf_init: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        release(c);
+        return fail(nullptr, oom ? NF_ENOMEM : NF_ECUDA, m);
+    }
+    memset(c->state_h, 0, sizeof(nf::DevState));
+    c->tune = nf_tuning{2, 4, 0, 1};
+    if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1;
+    *out = reinterpret_cast<nf_ctx *>(c);
+    return NF_OK;
+}
+
+void nf_free(nf_ctx *ctx) { release(reinterpret_cast<Ctx *>(ctx)); }
+
+int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double mass_if_null,
+                     int64_t n, const int64_t *box_offsets, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_bin_particles: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    c->binned = 0;
+    if (n < 0 || n > c->capacity) return fail(c, NF_EINVAL, "nf_bin_particles: n must be in [0, capacity]");
+    if (n > 0 && !pos) return fail(c, NF_EINVAL, "nf_bin_particles: pos is NULL");
+    if (!mass && !(std::isfinite(mass_if_null))) return fail(c, NF_EINVAL, "nf_bin_particles: mass_if_null must be finite");
+    std::vector<int64_t> poff(c->n_boxes + 1);
+    if (c->n_boxes == 1) {
+        if (box_offsets && (box_offsets[0] != 0 || box_offsets[1] != n))
+            return fail(c, NF_EINVAL, "nf_bin_particles: box_offsets must be {0, n}");
+        poff[0] = 0;
+        poff[1] = n;
+    } else {
+        if (!box_offsets) return fail(c, NF_EINVAL, "nf_bin_particles: box_offsets required for n_boxes > 1");
+        if (box_offsets[0] != 0 || box_offsets[c->n_boxes] != n)
+            return fail(c, NF_EINVAL, "nf_bin_particles: box_offsets must start at 0 and end at n");
+        for (int b = 0; b < c->n_boxes; ++b) {
+            if (box_offsets[b + 1] < box_offsets[b])
+                return fail(c, NF_EINVAL, "nf_bin_particles: box_offsets must be non-decreasing");
+            poff[b] = box_offsets[b];
+        }
+        poff[c->n_boxes] = n;
+    }
+    if (poff != c->poff_h) {
+        NF_CK(c, cudaStreamSynchronize(s));
+        NF_CK(c, cudaMemcpy(c->poff_d, poff.data(), sizeof(int64_t) * poff.size(), cudaMemcpyHostToDevice));
+        c->poff_h = poff;
+    }
+    c->equal_mass = mass ? 0 : 1;
+    c->m0 = (float)mass_if_null;
+    NF_CK(c, cudaEventRecord(c->ev_bin0, s));
+    cudaError_t e = nf::launch_bin(c, pos, mass, c->m0, n, s);
+    if (e) return cuda_fail(c, e, "nf_bin_particles");
+    NF_CK(c, cudaEventRecord(c->ev_bin1, s));
+    c->have_bin_time = 1;
+    NF_CK(c, cudaMemcpyAsync(&c->state_h->error, &c->state->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaStreamSynchronize(s));
+    c->n = n;
+    c->last_stream = s;
+    if (c->state_h->error) {
+        return fail(c, NF_ERANGE, "nf_bin_particles: a position component is not finite or outside [0, L)");
+    }
+    c->binned = 1;
+    c->have_momentum = 0;
+    return NF_OK;
+}
+
+int nf_compute_accel(nf_ctx *ctx, float *acc, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_accel: ctx is NULL");
+    DeviceGuard guard(c->device);
+    return compute_forward(c, acc, 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int nf_compute_accel_f64(nf_ctx *ctx, double *acc, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_accel_f64: ctx is NULL");
+    DeviceGuard guard(c->device);
+    return compute_forward(c, acc, 1, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_accel_vjp: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_vjp: no binned particles");
+    if (c->n > 0 && (!w || !grad_pos)) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: w and grad_pos are required");
+    int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
+    if (rc) return rc;
+    cudaError_t e;
+    if (c->tune.use_graph) {
+        std::vector<uint64_t> key = {(uint64_t)(uintptr_t)w, (uint64_t)(uintptr_t)grad_pos, (uint64_t)c->n,
+                                     (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
+                                     (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
+                                     (uint64_t)c->equal_mass};
+        e = run_graph(c, c->g_vjp, key, [&](cudaStream_t cs) { return enqueue_vjp(c, w, grad_pos, cs); }, s);
+    } else {
+        e = enqueue_vjp(c, w, grad_pos, s);
+    }
+    if (e) return cuda_fail(c, e, "nf_compute_accel_vjp");
+    c->have_pair_time = 1;
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, double mass_if_null,
+                  int64_t n, const int64_t *box_offsets, float *acc_host, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_accel_host: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n < 0 || n > c->capacity) return fail(c, NF_EINVAL, "nf_accel_host: n must be in [0, capacity]");
+    if (n > 0 && (!pos_host || !acc_host)) return fail(c, NF_EINVAL, "nf_accel_host: pos_host and acc_host are required");
+    if (n > c->st_cap || (mass_host && !c->st_mass)) {
+        NF_CK(c, cudaStreamSynchronize(s));
+        cudaFree(c->st_pos); cudaFree(c->st_acc); cudaFree(c->st_mass);
+        c->st_pos = c->st_acc = c->st_mass = nullptr;
+        c->st_cap = 0;
+        const int64_t m = n > 0 ? n : 1;
+        cudaError_t e = dalloc(&c->st_pos, 3 * m);
+        if (!e) e = dalloc(&c->st_acc, 3 * m);
+        if (!e) e = dalloc(&c->st_mass, m);
+        if (e) { cudaGetLastError(); return fail(c, NF_ENOMEM, "nf_accel_host: staging allocation failed"); }
+        c->st_cap = m;
+    }
+    if (n > 0) {
+        NF_CK(c, cudaMemcpyAsync(c->st_pos, pos_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        if (mass_host)
+            NF_CK(c, cudaMemcpyAsync(c->st_mass, mass_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+    }
+    int rc = nf_bin_particles(ctx, c->st_pos, mass_host ? c->st_mass : nullptr, mass_if_null, n,
+                              box_offsets, stream);
+    if (rc) return rc;
+    rc = nf_compute_accel(ctx, c->st_acc, stream);
+    if (rc) return rc;
+    if (n > 0)
+        NF_CK(c, cudaMemcpyAsync(acc_host, c->st_acc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaStreamSynchronize(s));
+    return NF_OK;
+}
+
+int nf_copy_binning(nf_ctx *ctx, int32_t *cell_start, int32_t *perm, float *sorted, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_copy_binning: ctx is NULL");
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_copy_binning: no binned particles");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (cell_start)
+        NF_CK(c, cudaMemcpyAsync(cell_start, c->cell_start, sizeof(int) * (c->n_cells + 1),
+                                 cudaMemcpyDeviceToDevice, s));
+    if (c->n > 0 && perm)
+        NF_CK(c, cudaMemcpyAsync(perm, c->perm, sizeof(int) * c->n, cudaMemcpyDeviceToDevice, s));
+    if (c->n > 0 && sorted)
+        NF_CK(c, cudaMemcpyAsync(sorted, c->sorted, sizeof(float4) * c->n, cudaMemcpyDeviceToDevice, s));
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !out) return fail(c, NF_EINVAL, "nf_get_stats: ctx and out are required");
+    DeviceGuard guard(c->device);
+    NF_CK(c, cudaStreamSynchronize(c->last_stream));
+    out->n_particles = c->binned ? c->n : 0;
+    out->n_cells = c->n_cells;
+    out->interactions = (int64_t)c->state_h->interactions;
+    out->max_occupancy = c->state_h->max_occ;
+    out->n_items = c->state_h->n_items;
+    for (int a = 0; a < 3; ++a) out->momentum[a] = c->have_momentum ? c->mom_h[a] : 0.0;
+    out->abs_momentum = c->have_momentum ? c->mom_h[3] : 0.0;
+    float ms = 0.f;
+    out->bin_ms = (c->have_bin_time && cudaEventElapsedTime(&ms, c->ev_bin0, c->ev_bin1) == cudaSuccess) ? ms : 0.0;
+    ms = 0.f;
+    out->pair_ms = (c->have_pair_time && cudaEventElapsedTime(&ms, c->ev_pair0, c->ev_pair1) == cudaSuccess) ? ms : 0.0;
+    cudaGetLastError();
+    out->kernel_launches = c->launches;
+    return NF_OK;
+}
+
+int nf_set_tuning(nf_ctx *ctx, const nf_tuning *t) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !t) return fail(c, NF_EINVAL, "nf_set_tuning: ctx and t are required");
+    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32]");
+    if (c->precision == NF_PREC_FP64_REF && t->sinks_per_lane != 1)
+        return fail(c, NF_EINVAL, "nf_set_tuning: FP64 reference contexts use one sink per lane");
+    c->tune = *t;
+    return NF_OK;
+}
+
+int nf_get_tuning(const nf_ctx *ctx, nf_tuning *t) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c || !t) return NF_EINVAL;
+    *t = c->tune;
+    return NF_OK;
+}
+
+int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_autotune: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_autotune: no binned particles");
+    if (reps < 1) reps = 1;
+    std::vector<nf_tuning> cands;
+    const int ks[] = {1, 2, 4};
+    const int ws[] = {4, 8};
+    for (int k : ks) {
+        if (c->precision == NF_PREC_FP64_REF && k != 1) continue;
+        for (int w : ws) cands.push_back(nf_tuning{k, w, 0, c->tune.use_graph});
+    }
+    float *acc = nullptr;
+    NF_CK(c, dalloc(&acc, 3 * (c->n > 0 ? c->n : 1)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const nf_tuning saved = c->tune;
+    float best_ms = 1e30f;
+    nf_tuning best_t = saved;
+    int rc = NF_OK;
+    for (const nf_tuning &t : cands) {
+        c->tune = t;
+        c->tune.use_graph = 0;
+        if ((rc = ensure_decomp(c, t.sinks_per_lane, s))) break;
+        cudaError_t e = nf::launch_worklist(c, s);
+        if (!e) e = nf::launch_pairs(c, acc, 0, c->tune, s);   // warm-up
+        if (e) { rc = cuda_fail(c, e, "nf_autotune"); break; }
+        float tot = 0.f;
+        for (int r = 0; r < reps && !e; ++r) {
+            e = nf::launch_worklist(c, s);
+            if (!e) e = cudaEventRecord(e0, s);
+            if (!e) e = nf::launch_pairs(c, acc, 0, c->tune, s);
+            if (!e) e = cudaEventRecord(e1, s);
+            if (!e) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+            tot += ms;
+        }
+        if (e) { rc = cuda_fail(c, e, "nf_autotune"); break; }
+        if (tot < best_ms) { best_ms = tot; best_t = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(acc);
+    best_t.use_graph = saved.use_graph;
+    c->tune = rc ? saved : best_t;
+    if (!rc && best) *best = best_t;
+    c->last_stream = s;
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+// nf_bin.cu -- cell binning (the cubic cell lattice of Maksimova et al. 2021,
+// Sec. 3.1): per-particle cell id, per-cell count, exclusive prefix scan,
+// stable sort by cell (LSD radix sort whose digit ranks keep input order) and
+// the gather into cell-sorted float4 records of cell-relative coordinates.
+//
+// Cell arithmetic, identical on every device and host: u = (x * CPD) / L in
+// IEEE double with no contraction, cell = floor(u) (CPD rounds down to
+// CPD-1), relative coordinate float32(u - (cell + 0.5)) in cell units.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nf_ctx.h"
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;                       // per thread
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kRadixThreads = 256;                  // 8 warps
+constexpr int kRadixItems = 16;                     // chunks of 32 per warp
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096 keys
+constexpr int kRadixDigits = 256;
+
+__device__ __forceinline__ int box_of_particle(const int64_t *poff, int n_boxes, int64_t i) {
+    int lo = 0, hi = n_boxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (poff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// u = (x * CPD) / L. When L is a power of two the division is exact and
+// equals multiplication by 1/L, which avoids the FP64 divide.
+__device__ __forceinline__ double cell_unit(double x, const BoxDev &B, bool pow2) {
+    double p = __dmul_rn(x, B.cpd_d);
+    return pow2 ? __dmul_rn(p, 1.0 / B.L) : __ddiv_rn(p, B.L);
+}
+
+__device__ __forceinline__ int cell_index(double u, int cpd) {
+    int c = (int)floor(u);
+    return c >= cpd ? cpd - 1 : c;
+}
+
+// a1 + a2: cell id of every particle and per-cell counts.
+__global__ void k_cell_ids(const float *__restrict__ pos, int64_t n,
+                           const int64_t *__restrict__ poff, int n_boxes,
+                           const BoxDev *__restrict__ boxes, int pow2,
+                           int *__restrict__ cid, int *__restrict__ count,
+                           DevState *st) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool live = i < n;
+        int cell = -1;
+        if (live) {
+            const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
+            const BoxDev B = boxes[b];
+            int c3[3];
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double x = (double)pos[3 * i + a];
+                const bool in = (x >= 0.0) && (x < B.L);   // false for NaN
+                ok = ok && in;
+                c3[a] = in ? cell_index(cell_unit(x, B, pow2 != 0), B.cpd) : 0;
+            }
+            if (!ok) atomicOr(&st->error, 1);
+            cell = B.cell_off + (c3[0] * B.cpd + c3[1]) * B.cpd + c3[2];
+            cid[i] = cell;
+        }
+        // warp-aggregated histogram: particles in input order are often
+        // spatially coherent, so many lanes hit the same counter
+        const unsigned live_mask = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const unsigned peers = __match_any_sync(live_mask, cell);
+            if (lane == __ffs(peers) - 1) atomicAdd(&count[cell], __popc(peers));
+        }
+    }
+}
+
+// ------------------------------------------------------------ scan
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int block_excl_scan(int v, int &excl) {
+    __shared__ int warp_tot[32];
+    __shared__ int block_tot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    int inc = warp_incl_scan(v);
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nw ? warp_tot[lane] : 0;
+        int ti = warp_incl_scan(t);
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == 31) block_tot = ti;     // lane 31 holds the inclusive total
+    }
+    __syncthreads();
+    excl = warp_tot[warp] + inc - v;
+    int total = block_tot;
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_scan_reduce(const int *__restrict__ in, int64_t n, int *__restrict__ block_sum) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    int excl;
+    int tot = block_excl_scan(s, excl);
+    if (threadIdx.x == 0) block_sum[blockIdx.x] = tot;
+}
+
+// One block scans up to kScanThreads * 8 block sums in place; writes the
+// grand total to *total.
+__global__ void k_scan_blocks(int *__restrict__ block_sum, int nb, int *__restrict__ total) {
+    constexpr int P = 8;
+    int v[P];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        int idx = threadIdx.x * P + k;
+        v[k] = idx < nb ? block_sum[idx] : 0;
+        s += v[k];
+    }
+    int excl;
+    int tot = block_excl_scan(s, excl);
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        int idx = threadIdx.x * P + k;
+        if (idx < nb) block_sum[idx] = excl;
+        excl += v[k];
+    }
+    if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, int64_t n,
+                             const int *__restrict__ block_off, int *__restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int excl;
+    block_excl_scan(s, excl);
+    excl += block_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = excl;
+        excl += v[k];
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Digit histogram of one tile; hist is digit-major: hist[d * ntiles + tile].
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_upsweep(const int *__restrict__ keys, int64_t n, int shift, int64_t ntiles,
+                int *__restrict__ hist) {
+    __shared__ int h[kRadixDigits];
+    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * (32 * kRadixItems);
+#pragma unroll 4
+    for (int c = 0; c < kRadixItems; ++c) {
+        const int64_t idx = base + c * 32 + lane;
+        const bool live = idx < n;
+        const int d = live ? ((keys[idx] >> shift) & 0xff) : (0x100 + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (live && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x)
+        hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Stable scatter of one tile: warps own consecutive sub-tiles, chunks of 32
+// are ranked in order with match_any, so equal digits keep input order.
+// vals_in == nullptr means the identity (first pass).
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_downsweep(const int *__restrict__ keys_in, const int *__restrict__ vals_in, int64_t n,
+                  int shift, int64_t ntiles, const int *__restrict__ hist_scanned,
+                  int *__restrict__ keys_out, int *__restrict__ vals_out, int write_keys) {
+    __shared__ int woff[kRadixWarps][kRadixDigits];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += blockDim.x)
+        (&woff[0][0])[d] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * (32 * kRadixItems);
+    int key[kRadixItems], dig[kRadixItems];
+#pragma unroll
+    for (int c = 0; c < kRadixItems; ++c) {
+        const int64_t idx = base + c * 32 + lane;
+        const bool live = idx < n;
+        key[c] = live ? keys_in[idx] : 0;
+        dig[c] = live ? ((key[c] >> shift) & 0xff) : (0x100 + lane);
+    }
+    // per-warp digit counts
+#pragma unroll
+    for (int c = 0; c < kRadixItems; ++c) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
+        if (dig[c] < 0x100 && lane == __ffs(peers) - 1) woff[warp][dig[c]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive scan over warps per digit, plus the tile's global base
+    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x) {
+        int run = hist_scanned[(int64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < kRadixWarps; ++w) {
+            int t = woff[w][d];
+            woff[w][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int c = 0; c < kRadixItems; ++c) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
+        const bool live = dig[c] < 0x100;
+        int dest = 0;
+        if (live) dest = woff[warp][dig[c]] + __popc(peers & lt);
+        __syncwarp();
+        if (live && lane == __ffs(peers) - 1) woff[warp][dig[c]] += __popc(peers);
+        __syncwarp();
+        if (live) {
+            const int64_t idx = base + c * 32 + lane;
+            const int v = vals_in ? vals_in[idx] : (int)idx;
+            if (write_keys) keys_out[dest] = key[c];
+            vals_out[dest] = v;
+        }
+    }
+}
+
+// a4 + a5: sorted record k = particle perm[k]: cell-relative coordinates in
+// cell units and its mass.
+__global__ void k_gather(const float *__restrict__ pos, const float *__restrict__ mass, float m0,
+                         int64_t n, const int *__restrict__ perm,
+                         const int64_t *__restrict__ poff, int n_boxes,
+                         const BoxDev *__restrict__ boxes, int pow2,
+                         float4 *__restrict__ sorted, dbl4 *__restrict__ sorted_d) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int i = perm[k];
+        const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
+        const BoxDev B = boxes[b];
+        double r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double x = (double)pos[3 * (int64_t)i + a];
+            const bool in = (x >= 0.0) && (x < B.L);
+            const double u = in ? cell_unit(x, B, pow2 != 0) : 0.5;
+            const int c = in ? cell_index(u, B.cpd) : 0;
+            r[a] = __dsub_rn(u, (double)c + 0.5);
+        }
+        const float m = mass ? mass[i] : m0;
+        sorted[k] = make_float4(__double2float_rn(r[0]), __double2float_rn(r[1]),
+                                __double2float_rn(r[2]), m);
+        if (sorted_d) sorted_d[k] = dbl4_make(r[0], r[1], r[2], (double)m);
+    }
+}
+
+int grid_for(int64_t n, int threads, int sm_count, int per_sm = 8) {
+    int64_t g = (n + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total. tmp holds
+// ceil(n / kScanTile) + 1 ints. Requires ceil(n / kScanTile) <= 8192.
+cudaError_t scan_exclusive(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s,
+                           int64_t *launches) {
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb > kScanThreads * 8) return cudaErrorInvalidValue;
+    if (launches) *launches += 3;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_blocks<<<1, kScanThreads, 0, s>>>(tmp, (int)nb, out + n);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, out);
+    return cudaGetLastError();
+}
+
+int64_t scan_tmp_ints(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+int64_t radix_tiles(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
+                       cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->count, 0, sizeof(int) * c->n_cells, s))) return e;
+    if ((e = cudaMemsetAsync(&c->state->error, 0, sizeof(int), s))) return e;
+    if (n > 0) {
+        k_cell_ids<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(
+            pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, c->keys_a, c->count, c->state);
+        if ((e = cudaGetLastError())) return e;
+        c->launches += 1;
+    }
+    if ((e = scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches))) return e;
+    if (n == 0) {
+        c->perm = c->vals_a;
+        return cudaSuccess;
+    }
+    // passes of 8 bits over the used key bits
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < c->n_cells) ++bits;
+    const int passes = bits <= 8 ? 1 : (bits + 7) / 8;
+    const int64_t nt = radix_tiles(n);
+    int *kin = c->keys_a, *kout = c->keys_b;
+    int *vin = nullptr, *vout = c->vals_a;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_radix_upsweep<<<(unsigned)nt, kRadixThreads, 0, s>>>(kin, n, shift, nt, c->radix_hist);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = scan_exclusive(c->radix_hist, c->radix_hist, nt * kRadixDigits, c->scan_tmp, s,
+                                    &c->launches)))
+            return e;
+        const int last = p == passes - 1;
+        k_radix_downsweep<<<(unsigned)nt, kRadixThreads, 0, s>>>(
+            kin, vin, n, shift, nt, c->radix_hist, kout, vout, !last);
+        if ((e = cudaGetLastError())) return e;
+        c->launches += 2;
+        // ping-pong
+        int *t = kin; kin = kout; kout = t;
+        vin = vout;
+        vout = (vout == c->vals_a) ? c->vals_b : c->vals_a;
+    }
+    c->perm = vin;
+    k_gather<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(
+        pos, mass, m0, n, c->perm, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, c->sorted,
+        c->precision == NF_PREC_FP64_REF ? c->sorted_d : nullptr);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace nf

@@ -1,0 +1,89 @@
+// nf_ctx.h -- host-side context of libnf (one per nf_init).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nf_internal.cuh"
+
+namespace nf {
+
+// A captured phase of work replayed as a CUDA graph; `key` holds the
+// arguments baked into the capture.
+struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> key;
+    int64_t n_kernels = 0;        // kernels per replay
+};
+
+struct Ctx {
+    int device = 0;
+    int n_boxes = 0;
+    int R = 2;
+    int precision = NF_PREC_FP32;
+    int64_t capacity = 0;
+    int64_t n_cells = 0;          // total over boxes
+    int sm_count = 0;
+    int pow2_all = 0;             // every box side is a power of two
+
+    std::vector<BoxDev> boxes_h;
+    BoxDev *boxes_d = nullptr;
+    int64_t *poff_d = nullptr;    // particle offsets per box [n_boxes+1]
+    std::vector<int64_t> poff_h;
+
+    // binning
+    int *keys_a = nullptr, *keys_b = nullptr;     // [capacity]
+    int *vals_a = nullptr, *vals_b = nullptr;     // [capacity]
+    int *perm = nullptr;                           // alias of the final values buffer
+    int *count = nullptr;                          // [n_cells]
+    int *cell_start = nullptr;                     // [n_cells + 1]
+    int *scan_tmp = nullptr;                       // block sums of the scans
+    int *radix_hist = nullptr;                     // [256 * max_tiles + 1]
+    int64_t max_tiles = 0;
+    float4 *sorted = nullptr;                      // [capacity] (rx, ry, rz, m)
+    dbl4 *sorted_d = nullptr;                   // [capacity] FP64 copy (FP64_REF only)
+    float4 *w_sorted = nullptr;                    // [capacity] VJP cotangent, sorted
+
+    // work list
+    int *nsrc_cell = nullptr;                      // [n_cells]
+    WorkItem *items = nullptr;                     // [capacity]
+    Decomp *decomp_d = nullptr;
+    int decomp_k = 0;
+    DevState *state = nullptr;
+    DevState *state_h = nullptr;                   // pinned mirror
+
+    // momentum diagnostic
+    double *mom_partial = nullptr;                 // [kMomBlocks * 4]
+    double *mom_result = nullptr;                  // [4]
+    double *mom_h = nullptr;                       // pinned [4]
+
+    // last binning
+    int64_t n = 0;
+    int binned = 0;
+    int equal_mass = 1;
+    float m0 = 0.f;
+    int have_momentum = 0;
+
+    nf_tuning tune{2, 4, 0, 1};
+    cudaStream_t cap_stream = nullptr;             // private capture stream
+    GraphSlot g_fwd, g_vjp;
+    cudaStream_t last_stream = nullptr;
+
+    // host-buffer staging for nf_accel_host
+    float *st_pos = nullptr, *st_mass = nullptr, *st_acc = nullptr;
+    int64_t st_cap = 0;
+
+    // timing of the last binning / pair kernel, and the launch counter
+    cudaEvent_t ev_bin0 = nullptr, ev_bin1 = nullptr, ev_pair0 = nullptr, ev_pair1 = nullptr;
+    int64_t launches = 0;
+    int have_bin_time = 0, have_pair_time = 0;
+
+    std::string err;
+};
+
+constexpr int kMomBlocks = 512;
+
+}  // namespace nf

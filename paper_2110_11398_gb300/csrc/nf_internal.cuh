@@ -1,0 +1,147 @@
+// nf_internal.cuh -- device-side structures and helpers shared by the libnf
+// translation units (binning, work list, pair kernels, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nf.h"
+
+namespace nf {
+
+// Largest supported near-field radius (neighbourhood of (2R+1)^3 cells).
+constexpr int kMaxRadius = 3;
+constexpr int kMaxNbr = (2 * kMaxRadius + 1) * (2 * kMaxRadius + 1) * (2 * kMaxRadius + 1);
+// Sources staged per warp tile.
+constexpr int kTile = 128;
+// Number of cost buckets of the work list (heaviest items are served first).
+constexpr int kBuckets = 64;
+// Max items one remainder of a cell can be cut into (see make_decomp()).
+constexpr int kDecompMax = 8;
+
+// Four doubles, 32-byte aligned (cell-sorted FP64 record x, y, z, m).
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dbl4 dbl4_make(double x, double y, double z, double w) {
+    dbl4 r;
+    r.x = x; r.y = y; r.z = z; r.w = w;
+    return r;
+}
+
+// Per-box constants. Coordinates inside the library are in cell units
+// (h = L / CPD = 1); the epilogue scales back to the caller's units.
+struct BoxDev {
+    double L;          // box side (caller units)
+    double cpd_d;      // CPD as double (binning arithmetic)
+    double eps2_d;     // (eps / h)^2
+    double inv_h2_d;   // 1 / h^2
+    double inv_h3_d;   // 1 / h^3
+    int cpd;           // cells per dimension
+    int cell_off;      // global id of this box's first cell
+    float eps2;        // (eps / h)^2, FP32
+    float inv_h2;      // 1 / h^2, FP32
+    float inv_h3;      // 1 / h^3, FP32
+    int pad;
+};
+
+// One unit of pair work: `n` consecutive cell-sorted sinks of one cell,
+// processed by one warp whose lanes are split `1 << log2s` ways over sources.
+struct __align__(16) WorkItem {
+    int cell;      // global cell id of the sinks
+    int first;     // first sorted slot of the sinks
+    int n;         // number of sinks (<= 32 * K >> log2s)
+    int box_s;     // (box << 8) | log2s
+};
+
+// Device-resident counters of one context.
+struct DevState {
+    int error;                   // bit 0: a position outside [0, L) or not finite
+    int n_items;                 // items written by the last work-list build
+    int queue_head;              // persistent-kernel work counter
+    int max_occ;                 // largest cell population
+    unsigned long long interactions;
+    int bucket_count[kBuckets];
+    int bucket_cursor[kBuckets];
+};
+
+// Decomposition of a cell's remainder of sinks into items: entry r lists
+// (count, log2s) pairs; see make_decomp() in nf_pairs.cu.
+struct Decomp {
+    int n_entries[128];
+    int entry[128][kDecompMax];  // (count << 8) | log2s
+};
+
+// ------------------------------------------------------------ packed FP32
+// Blackwell executes two FP32 lanes per instruction with the .f32x2 forms
+// (PTX ISA 8.6+, sm_100a family). A packed value is a 64-bit register pair
+// {lo, hi}.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b) {
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b) {
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// Hardware reciprocal square root (MUFU), flush-to-zero: the PTX
+// rsqrt.approx.ftz.f32 instruction.
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ f2_t f2_rsqrt(f2_t v) {
+    float a, b;
+    f2_unpack(v, a, b);
+    return f2_pack(rsqrt_hw(a), rsqrt_hw(b));
+}
+
+__device__ __forceinline__ int box_of_cell(const BoxDev *boxes, int n_boxes, int cell) {
+    int lo = 0, hi = n_boxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (boxes[mid].cell_off <= cell) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace nf
+
+// Host-side entry points of each translation unit (C++ linkage, internal).
+namespace nf {
+struct Ctx;
+cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
+                       cudaStream_t s);
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s);
+cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s);
+cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);
+cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s);
+void make_decomp(int k, Decomp *d);
+cudaError_t scan_exclusive(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s,
+                           int64_t *launches);
+int64_t scan_tmp_ints(int64_t n);
+int64_t radix_tiles(int64_t n);
+}  // namespace nf

@@ -1,0 +1,949 @@
+// nf_pairs.cu -- work list and pair kernels of the near-field direct sum
+// (Maksimova et al. 2021, Sec. 3.1: every sink sums the particles of the
+// (2R+1)^3 cells around its own cell; Sec. 4.3/4.5: the GPU works through
+// queued units of sink x source cells).
+//
+// Work decomposition. A work item is a run of consecutive cell-sorted sinks
+// of one cell, served to one warp. The warp's lanes are split S ways over the
+// sources (lane = g * S + s; lane g holds K sinks g, g + 32/S, ...), so a cell
+// of n sinks costs ceil-ish(n / (32K/S)) items with little idle lane time.
+// Items are placed in cost buckets, heaviest first, and a persistent grid of
+// warps pulls them from an atomic counter.
+//
+// Pair loop. Coordinates are cell-relative in cell units. A source of
+// neighbour cell offset d is staged in shared memory already shifted into the
+// sink cell's frame (r_j + d), so one pair costs the 20 algorithmic flops of
+// the Plummer law: 3 sub, 3 fma (s = |D|^2 + eps^2), rsqrt, 2 mul (s^-3/2),
+// 3 fma (accumulate); masses are applied once per sink for equal-mass sets.
+// Two sources are processed per instruction with the packed .f32x2 forms.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nf_ctx.h"
+#include "nf_internal.cuh"
+
+namespace nf {
+
+namespace {
+
+constexpr float kFarAway = 1.0e18f;   // padding source: contributes exactly 0
+
+__device__ __forceinline__ int wrapc(int t, int cpd) {
+    t = t < 0 ? t + cpd : t;
+    return t >= cpd ? t - cpd : t;
+}
+
+__device__ __forceinline__ int cell_nsrc(const BoxDev &B, int local, const int *__restrict__ count,
+                                         int R) {
+    const int cpd = B.cpd;
+    const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
+    int s = 0;
+    for (int dx = -R; dx <= R; ++dx) {
+        const int x = wrapc(cx + dx, cpd);
+        for (int dy = -R; dy <= R; ++dy) {
+            const int row = B.cell_off + (x * cpd + wrapc(cy + dy, cpd)) * cpd;
+            for (int dz = -R; dz <= R; ++dz) s += count[row + wrapc(cz + dz, cpd)];
+        }
+    }
+    return s;
+}
+
+// Item cost model: each lane handles K sinks over n_src / S sources at ~11
+// packed-lane instructions per sink-source, plus staging; the bucket is the
+// number of leading zeros so that heavier items get smaller bucket indices.
+__device__ __forceinline__ int cost_bucket(int nsrc, int K, int log2s) {
+    unsigned long long cost = (unsigned long long)nsrc * (unsigned long long)((22 * K) >> log2s) +
+                              (unsigned long long)nsrc;
+    return __clzll(cost | 1ull);
+}
+
+struct WLArgs {
+    const BoxDev *boxes;
+    int n_boxes;
+    int R;
+    int K;
+    int64_t n_cells;
+    const int *count;
+    const int *cell_start;
+    int *nsrc_cell;
+    const Decomp *decomp;
+    DevState *st;
+    WorkItem *items;
+};
+
+__global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
+    __shared__ int hist[kBuckets];
+    __shared__ unsigned long long s_inter;
+    __shared__ int s_max;
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+    if (threadIdx.x == 0) { s_inter = 0; s_max = 0; }
+    __syncthreads();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long inter = 0;
+    int mx = 0;
+    if (c < a.n_cells) {
+        const int n = a.count[c];
+        if (n > 0) {
+            const int box = a.n_boxes == 1 ? 0 : box_of_cell(a.boxes, a.n_boxes, (int)c);
+            const BoxDev B = a.boxes[box];
+            const int ns = cell_nsrc(B, (int)c - B.cell_off, a.count, a.R);
+            a.nsrc_cell[c] = ns;
+            inter = (unsigned long long)n * (unsigned long long)ns;
+            mx = n;
+            const int full = 32 * a.K;
+            const int q = n / full, r = n % full;
+            if (q) atomicAdd(&hist[cost_bucket(ns, a.K, 0)], q);
+            for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
+                const int ent = a.decomp->entry[r][e];
+                atomicAdd(&hist[cost_bucket(ns, a.K, ent & 0xff)], 1);
+            }
+        }
+    }
+    // block reductions
+    for (int o = 16; o > 0; o >>= 1) {
+        inter += __shfl_xor_sync(0xffffffffu, inter, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (inter) atomicAdd(&s_inter, inter);
+        if (mx) atomicMax(&s_max, mx);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+        if (hist[b]) atomicAdd(&a.st->bucket_count[b], hist[b]);
+    if (threadIdx.x == 0) {
+        if (s_inter) atomicAdd(&a.st->interactions, s_inter);
+        if (s_max) atomicMax(&a.st->max_occ, s_max);
+    }
+}
+
+__global__ void k_wl_scan(DevState *st) {
+    // one warp: exclusive scan of the bucket counts
+    const int lane = threadIdx.x;
+    int run = 0;
+    for (int b0 = 0; b0 < kBuckets; b0 += 32) {
+        const int v = st->bucket_count[b0 + lane];
+        int inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        st->bucket_cursor[b0 + lane] = run + inc - v;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) {
+        st->n_items = run;
+        st->queue_head = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
+    __shared__ int cnt[kBuckets];
+    __shared__ int base[kBuckets];
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int n = 0, ns = 0, box = 0;
+    if (c < a.n_cells) {
+        n = a.count[c];
+        if (n > 0) {
+            box = a.n_boxes == 1 ? 0 : box_of_cell(a.boxes, a.n_boxes, (int)c);
+            ns = a.nsrc_cell[c];
+        }
+    }
+    const int full = 32 * a.K;
+    const int q = n / full, r = n % full;
+    if (n > 0) {
+        if (q) atomicAdd(&cnt[cost_bucket(ns, a.K, 0)], q);
+        for (int e = 0; e < a.decomp->n_entries[r]; ++e)
+            atomicAdd(&cnt[cost_bucket(ns, a.K, a.decomp->entry[r][e] & 0xff)], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+        base[b] = cnt[b] ? atomicAdd(&a.st->bucket_cursor[b], cnt[b]) : 0;
+        cnt[b] = 0;
+    }
+    __syncthreads();
+    if (n > 0) {
+        const int first = a.cell_start[c];
+        if (q) {
+            const int b = cost_bucket(ns, a.K, 0);
+            const int p = base[b] + atomicAdd(&cnt[b], q);
+            for (int j = 0; j < q; ++j) {
+                WorkItem w;
+                w.cell = (int)c;
+                w.first = first + j * full;
+                w.n = full;
+                w.box_s = box << 8;
+                a.items[p + j] = w;
+            }
+        }
+        int off = first + q * full;
+        for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
+            const int ent = a.decomp->entry[r][e];
+            const int b = cost_bucket(ns, a.K, ent & 0xff);
+            const int p = base[b] + atomicAdd(&cnt[b], 1);
+            WorkItem w;
+            w.cell = (int)c;
+            w.first = off;
+            w.n = ent >> 8;
+            w.box_s = (box << 8) | (ent & 0xff);
+            a.items[p] = w;
+            off += ent >> 8;
+        }
+    }
+}
+
+// ------------------------------------------------------------ pair kernels
+struct PairArgs {
+    const float4 *sorted;      // cell-sorted (rx, ry, rz, m)
+    const dbl4 *sorted_d;   // FP64 copy (FP64 kernel only)
+    const float4 *w_sorted;    // cell-sorted cotangent (VJP only)
+    const int *cell_start;
+    const int *perm;
+    const BoxDev *boxes;
+    const WorkItem *items;
+    DevState *st;
+    void *out;                 // N x 3, input order
+    int out_f64;
+    int R;
+    int nbr;                   // (2R+1)^3
+    int tbl;                   // per-warp table stride (ints), >= nbr + 1
+    float m0;                  // equal mass (when EQ)
+};
+
+// Per-warp neighbourhood table: pfx[ci] = exclusive prefix of the source
+// counts in cell order, dlt[ci] = cell_start - pfx (so source q of cell ci
+// sits at sorted slot q + dlt[ci]), ofs[ci] = packed cell offset d + R.
+// Returns the number of sources.
+__device__ __forceinline__ int build_table(const PairArgs &a, const BoxDev &B, int cell,
+                                           int *pfx, int *dlt, int *ofs) {
+    const int lane = threadIdx.x & 31;
+    const int cpd = B.cpd, R = a.R, W = 2 * R + 1;
+    const int local = cell - B.cell_off;
+    const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
+    int run = 0;
+    for (int b0 = 0; b0 < a.nbr; b0 += 32) {
+        const int ci = b0 + lane;
+        int cnt = 0, st = 0, code = 0;
+        if (ci < a.nbr) {
+            const int ix = ci / (W * W), iy = (ci / W) % W, iz = ci % W;
+            const int g = B.cell_off +
+                          (wrapc(cx + ix - R, cpd) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
+                          wrapc(cz + iz - R, cpd);
+            st = a.cell_start[g];
+            cnt = a.cell_start[g + 1] - st;
+            code = ix | (iy << 8) | (iz << 16);
+        }
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (ci < a.nbr) {
+            const int p = run + inc - cnt;
+            pfx[ci] = p;
+            dlt[ci] = st - p;
+            ofs[ci] = code;
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) pfx[a.nbr] = run;
+    __syncwarp();
+    return run;
+}
+
+// Source q of the item -> (sorted slot, offset code); `ci` is the lane's
+// running cell index (q only grows within an item).
+__device__ __forceinline__ int locate(const int *pfx, int nbr, int q, int &ci) {
+    while (ci + 1 < nbr && pfx[ci + 1] <= q) ++ci;
+    return ci;
+}
+
+__device__ __forceinline__ void two_sum(f2_t a, f2_t b, f2_t &s, f2_t &e) {
+    s = f2_add(a, b);
+    const f2_t bb = f2_sub(s, a);
+    e = f2_add(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb));
+}
+
+__device__ __forceinline__ void two_sum1(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Forward pair kernel. K sinks per lane; EQ: all masses equal (applied in
+// the epilogue); COMP: per-sink sums kept as compensated (hi, lo) pairs.
+template <int K, bool EQ, bool COMP>
+__global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    constexpr int NF = EQ ? 3 : 4;
+    float *sbase = reinterpret_cast<float *>(smem_raw) + wib * (NF * kTile + 3 * a.tbl);
+    float *sx = sbase, *sy = sbase + kTile, *sz = sbase + 2 * kTile, *sm = sbase + 3 * kTile;
+    int *pfx = reinterpret_cast<int *>(sbase + NF * kTile);
+    int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
+    const int n_items = a.st->n_items;
+
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.st->queue_head, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
+        const int S = 1 << log2s, G = 32 >> log2s;
+        const int g = lane >> log2s, sp = lane & (S - 1);
+        const BoxDev B = a.boxes[box];
+        const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
+        const f2_t eps2 = f2_pack(B.eps2, B.eps2);
+
+        f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K];
+        f2_t lx[K], ly[K], lz[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int si = g + G * k;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (si < w.n) p = a.sorted[w.first + si];
+            xi[k] = f2_pack(p.x, p.x);
+            yi[k] = f2_pack(p.y, p.y);
+            zi[k] = f2_pack(p.z, p.z);
+            ax[k] = ay[k] = az[k] = 0ull;
+            lx[k] = ly[k] = lz[k] = 0ull;
+        }
+        int ci = 0;
+        for (int q0 = 0; q0 < nsrc; q0 += kTile) {
+            const int cntT = min(kTile, nsrc - q0);
+            const int npair = (cntT + 1) >> 1;
+            for (int t = lane; t < 2 * npair; t += 32) {
+                const int q = q0 + t;
+                if (q < nsrc) {
+                    const int c = locate(pfx, a.nbr, q, ci);
+                    const float4 p = a.sorted[q + dlt[c]];
+                    const int code = ofs[c];
+                    sx[t] = p.x + (float)((code & 0xff) - a.R);
+                    sy[t] = p.y + (float)(((code >> 8) & 0xff) - a.R);
+                    sz[t] = p.z + (float)((code >> 16) - a.R);
+                    if (!EQ) sm[t] = p.w;
+                } else {
+                    sx[t] = kFarAway;
+                    sy[t] = 0.f;
+                    sz[t] = 0.f;
+                    if (!EQ) sm[t] = 0.f;
+                }
+            }
+            __syncwarp();
+            const f2_t *px = reinterpret_cast<const f2_t *>(sx);
+            const f2_t *py = reinterpret_cast<const f2_t *>(sy);
+            const f2_t *pz = reinterpret_cast<const f2_t *>(sz);
+            const f2_t *pm = reinterpret_cast<const f2_t *>(sm);
+#pragma unroll 2
+            for (int pp = sp; pp < npair; pp += S) {
+                const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
+                f2_t m2 = 0ull;
+                if (!EQ) m2 = pm[pp];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const f2_t dx = f2_sub(x2, xi[k]);
+                    const f2_t dy = f2_sub(y2, yi[k]);
+                    const f2_t dz = f2_sub(z2, zi[k]);
+                    f2_t s = f2_fma(dx, dx, eps2);
+                    s = f2_fma(dy, dy, s);
+                    s = f2_fma(dz, dz, s);
+                    const f2_t r = f2_rsqrt(s);
+                    f2_t f = f2_mul(f2_mul(r, r), r);
+                    if (!EQ) f = f2_mul(f, m2);
+                    if (!COMP) {
+                        ax[k] = f2_fma(f, dx, ax[k]);
+                        ay[k] = f2_fma(f, dy, ay[k]);
+                        az[k] = f2_fma(f, dz, az[k]);
+                    } else {
+                        f2_t e;
+                        two_sum(ax[k], f2_mul(f, dx), ax[k], e); lx[k] = f2_add(lx[k], e);
+                        two_sum(ay[k], f2_mul(f, dy), ay[k], e); ly[k] = f2_add(ly[k], e);
+                        two_sum(az[k], f2_mul(f, dz), az[k], e); lz[k] = f2_add(lz[k], e);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        // epilogue: fold the two packed halves, reduce over the S lanes of
+        // each sink group (xor tree, fixed order), scale and un-permute
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float v[3];
+            const f2_t hs[3] = {ax[k], ay[k], az[k]};
+            const f2_t ls[3] = {lx[k], ly[k], lz[k]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float h0, h1;
+                f2_unpack(hs[c], h0, h1);
+                if (!COMP) {
+                    float s = h0 + h1;
+                    for (int o = 1; o < S; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    v[c] = s;
+                } else {
+                    float l0, l1, h, e;
+                    f2_unpack(ls[c], l0, l1);
+                    two_sum1(h0, h1, h, e);
+                    float l = __fadd_rn(__fadd_rn(l0, l1), e);
+                    for (int o = 1; o < S; o <<= 1) {
+                        const float ho = __shfl_xor_sync(0xffffffffu, h, o);
+                        const float lo = __shfl_xor_sync(0xffffffffu, l, o);
+                        two_sum1(h, ho, h, e);
+                        l = __fadd_rn(__fadd_rn(l, lo), e);
+                    }
+                    v[c] = __fadd_rn(h, l);
+                }
+            }
+            const int si = g + G * k;
+            if (sp == 0 && si < w.n) {
+                const int i = a.perm[w.first + si];
+                if (a.out_f64) {
+                    const double sc = EQ ? (double)a.m0 * B.inv_h2_d : B.inv_h2_d;
+                    double *o = reinterpret_cast<double *>(a.out) + 3 * (int64_t)i;
+                    o[0] = (double)v[0] * sc;
+                    o[1] = (double)v[1] * sc;
+                    o[2] = (double)v[2] * sc;
+                } else {
+                    const float sc = EQ ? a.m0 * B.inv_h2 : B.inv_h2;
+                    float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+                    o[0] = v[0] * sc;
+                    o[1] = v[1] * sc;
+                    o[2] = v[2] * sc;
+                }
+            }
+        }
+    }
+}
+
+// FP64 reference pair kernel: same items and order of work, double
+// arithmetic throughout, s^-3/2 as 1 / (s * sqrt(s)). One sink per lane.
+__global__ void __launch_bounds__(512) k_pairs_f64(PairArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *sbase = reinterpret_cast<double *>(smem_raw) +
+                    wib * (4 * kTile + (3 * a.tbl + 1) / 2);
+    double *sx = sbase, *sy = sbase + kTile, *sz = sbase + 2 * kTile, *sm = sbase + 3 * kTile;
+    int *pfx = reinterpret_cast<int *>(sbase + 4 * kTile);
+    int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
+    const int n_items = a.st->n_items;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.st->queue_head, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
+        const int S = 1 << log2s;
+        const int g = lane >> log2s, sp = lane & (S - 1);
+        const BoxDev B = a.boxes[box];
+        const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
+        double xi = 0, yi = 0, zi = 0;
+        if (g < w.n) {
+            const dbl4 p = a.sorted_d[w.first + g];
+            xi = p.x; yi = p.y; zi = p.z;
+        }
+        double ax = 0, ay = 0, az = 0;
+        int ci = 0;
+        for (int q0 = 0; q0 < nsrc; q0 += kTile) {
+            const int cntT = min(kTile, nsrc - q0);
+            for (int t = lane; t < cntT; t += 32) {
+                const int q = q0 + t;
+                const int c = locate(pfx, a.nbr, q, ci);
+                const dbl4 p = a.sorted_d[q + dlt[c]];
+                const int code = ofs[c];
+                sx[t] = p.x + (double)((code & 0xff) - a.R);
+                sy[t] = p.y + (double)(((code >> 8) & 0xff) - a.R);
+                sz[t] = p.z + (double)((code >> 16) - a.R);
+                sm[t] = p.w;
+            }
+            __syncwarp();
+            for (int j = sp; j < cntT; j += S) {
+                const double dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
+                const double s = dx * dx + dy * dy + dz * dz + B.eps2_d;
+                const double f = sm[j] / (s * sqrt(s));
+                ax += f * dx;
+                ay += f * dy;
+                az += f * dz;
+            }
+            __syncwarp();
+        }
+        for (int o = 1; o < S; o <<= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+        }
+        if (sp == 0 && g < w.n) {
+            const int i = a.perm[w.first + g];
+            const double sc = B.inv_h2_d;
+            if (a.out_f64) {
+                double *o = reinterpret_cast<double *>(a.out) + 3 * (int64_t)i;
+                o[0] = ax * sc; o[1] = ay * sc; o[2] = az * sc;
+            } else {
+                float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+                o[0] = (float)(ax * sc); o[1] = (float)(ay * sc); o[2] = (float)(az * sc);
+            }
+        }
+    }
+}
+
+// Adjoint (vector-Jacobian product) pair kernel:
+//   g_k = sum_j J(D)(m_k w_j - m_j w_k),  J(D) u = s^-3/2 u - 3 s^-5/2 D (D.u)
+// accumulated as G1 = sum s^-3/2 u and G2 = sum s^-5/2 (D.u) D, g = G1 - 3 G2.
+template <int K, bool EQ>
+__global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    constexpr int NF = EQ ? 6 : 7;
+    float *sbase = reinterpret_cast<float *>(smem_raw) + wib * (NF * kTile + 3 * a.tbl);
+    float *sx = sbase, *sy = sbase + kTile, *sz = sbase + 2 * kTile;
+    float *swx = sbase + 3 * kTile, *swy = sbase + 4 * kTile, *swz = sbase + 5 * kTile;
+    float *sm = sbase + 6 * kTile;
+    int *pfx = reinterpret_cast<int *>(sbase + NF * kTile);
+    int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
+    const int n_items = a.st->n_items;
+
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.st->queue_head, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
+        const int S = 1 << log2s, G = 32 >> log2s;
+        const int g = lane >> log2s, sp = lane & (S - 1);
+        const BoxDev B = a.boxes[box];
+        const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
+        const f2_t eps2 = f2_pack(B.eps2, B.eps2);
+
+        f2_t xi[K], yi[K], zi[K], wxi[K], wyi[K], wzi[K], mi[K];
+        f2_t g1x[K], g1y[K], g1z[K], g2x[K], g2y[K], g2z[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int si = g + G * k;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f), wv = p;
+            if (si < w.n) {
+                p = a.sorted[w.first + si];
+                wv = a.w_sorted[w.first + si];
+            }
+            xi[k] = f2_pack(p.x, p.x); yi[k] = f2_pack(p.y, p.y); zi[k] = f2_pack(p.z, p.z);
+            wxi[k] = f2_pack(wv.x, wv.x); wyi[k] = f2_pack(wv.y, wv.y); wzi[k] = f2_pack(wv.z, wv.z);
+            mi[k] = f2_pack(p.w, p.w);
+            g1x[k] = g1y[k] = g1z[k] = g2x[k] = g2y[k] = g2z[k] = 0ull;
+        }
+        int ci = 0;
+        for (int q0 = 0; q0 < nsrc; q0 += kTile) {
+            const int cntT = min(kTile, nsrc - q0);
+            const int npair = (cntT + 1) >> 1;
+            for (int t = lane; t < 2 * npair; t += 32) {
+                const int q = q0 + t;
+                if (q < nsrc) {
+                    const int c = locate(pfx, a.nbr, q, ci);
+                    const int j = q + dlt[c];
+                    const float4 p = a.sorted[j];
+                    const float4 wv = a.w_sorted[j];
+                    const int code = ofs[c];
+                    sx[t] = p.x + (float)((code & 0xff) - a.R);
+                    sy[t] = p.y + (float)(((code >> 8) & 0xff) - a.R);
+                    sz[t] = p.z + (float)((code >> 16) - a.R);
+                    swx[t] = wv.x; swy[t] = wv.y; swz[t] = wv.z;
+                    if (!EQ) sm[t] = p.w;
+                } else {
+                    sx[t] = kFarAway; sy[t] = 0.f; sz[t] = 0.f;
+                    swx[t] = 0.f; swy[t] = 0.f; swz[t] = 0.f;
+                    if (!EQ) sm[t] = 0.f;
+                }
+            }
+            __syncwarp();
+            const f2_t *px = reinterpret_cast<const f2_t *>(sx);
+            const f2_t *py = reinterpret_cast<const f2_t *>(sy);
+            const f2_t *pz = reinterpret_cast<const f2_t *>(sz);
+            const f2_t *pwx = reinterpret_cast<const f2_t *>(swx);
+            const f2_t *pwy = reinterpret_cast<const f2_t *>(swy);
+            const f2_t *pwz = reinterpret_cast<const f2_t *>(swz);
+            const f2_t *pm = reinterpret_cast<const f2_t *>(sm);
+            for (int pp = sp; pp < npair; pp += S) {
+                const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
+                const f2_t wx2 = pwx[pp], wy2 = pwy[pp], wz2 = pwz[pp];
+                f2_t m2 = 0ull;
+                if (!EQ) m2 = pm[pp];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const f2_t dx = f2_sub(x2, xi[k]);
+                    const f2_t dy = f2_sub(y2, yi[k]);
+                    const f2_t dz = f2_sub(z2, zi[k]);
+                    f2_t s = f2_fma(dx, dx, eps2);
+                    s = f2_fma(dy, dy, s);
+                    s = f2_fma(dz, dz, s);
+                    const f2_t r = f2_rsqrt(s);
+                    const f2_t r2 = f2_mul(r, r);
+                    const f2_t r3 = f2_mul(r2, r);
+                    const f2_t r5 = f2_mul(r3, r2);
+                    f2_t ux, uy, uz;
+                    if (EQ) {
+                        ux = f2_sub(wx2, wxi[k]);
+                        uy = f2_sub(wy2, wyi[k]);
+                        uz = f2_sub(wz2, wzi[k]);
+                    } else {
+                        // m_k w_j - m_j w_k
+                        ux = f2_sub(f2_mul(mi[k], wx2), f2_mul(m2, wxi[k]));
+                        uy = f2_sub(f2_mul(mi[k], wy2), f2_mul(m2, wyi[k]));
+                        uz = f2_sub(f2_mul(mi[k], wz2), f2_mul(m2, wzi[k]));
+                    }
+                    f2_t du = f2_mul(dx, ux);
+                    du = f2_fma(dy, uy, du);
+                    du = f2_fma(dz, uz, du);
+                    const f2_t c = f2_mul(du, r5);
+                    g1x[k] = f2_fma(r3, ux, g1x[k]);
+                    g1y[k] = f2_fma(r3, uy, g1y[k]);
+                    g1z[k] = f2_fma(r3, uz, g1z[k]);
+                    g2x[k] = f2_fma(c, dx, g2x[k]);
+                    g2y[k] = f2_fma(c, dy, g2y[k]);
+                    g2z[k] = f2_fma(c, dz, g2z[k]);
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const f2_t g1[3] = {g1x[k], g1y[k], g1z[k]};
+            const f2_t g2[3] = {g2x[k], g2y[k], g2z[k]};
+            float v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float a0, a1, b0, b1;
+                f2_unpack(g1[c], a0, a1);
+                f2_unpack(g2[c], b0, b1);
+                float s1 = a0 + a1, s2 = b0 + b1;
+                for (int o = 1; o < S; o <<= 1) {
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                }
+                v[c] = s1 - 3.0f * s2;
+            }
+            const int si = g + G * k;
+            if (sp == 0 && si < w.n) {
+                const int i = a.perm[w.first + si];
+                const float sc = EQ ? a.m0 * B.inv_h3 : B.inv_h3;
+                float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+                o[0] = v[0] * sc;
+                o[1] = v[1] * sc;
+                o[2] = v[2] * sc;
+            }
+        }
+    }
+}
+
+// FP64 reference adjoint: one sink per lane, double arithmetic.
+__global__ void __launch_bounds__(512) k_vjp_f64(PairArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double *sbase = reinterpret_cast<double *>(smem_raw) +
+                    wib * (7 * kTile + (3 * a.tbl + 1) / 2);
+    double *sx = sbase, *sy = sbase + kTile, *sz = sbase + 2 * kTile;
+    double *swx = sbase + 3 * kTile, *swy = sbase + 4 * kTile, *swz = sbase + 5 * kTile;
+    double *sm = sbase + 6 * kTile;
+    int *pfx = reinterpret_cast<int *>(sbase + 7 * kTile);
+    int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
+    const int n_items = a.st->n_items;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(&a.st->queue_head, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
+        const int S = 1 << log2s;
+        const int g = lane >> log2s, sp = lane & (S - 1);
+        const BoxDev B = a.boxes[box];
+        const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
+        double xi = 0, yi = 0, zi = 0, mk = 0, wxk = 0, wyk = 0, wzk = 0;
+        if (g < w.n) {
+            const dbl4 p = a.sorted_d[w.first + g];
+            const float4 wv = a.w_sorted[w.first + g];
+            xi = p.x; yi = p.y; zi = p.z; mk = p.w;
+            wxk = wv.x; wyk = wv.y; wzk = wv.z;
+        }
+        double gx = 0, gy = 0, gz = 0;
+        int ci = 0;
+        for (int q0 = 0; q0 < nsrc; q0 += kTile) {
+            const int cntT = min(kTile, nsrc - q0);
+            for (int t = lane; t < cntT; t += 32) {
+                const int q = q0 + t;
+                const int c = locate(pfx, a.nbr, q, ci);
+                const int j = q + dlt[c];
+                const dbl4 p = a.sorted_d[j];
+                const float4 wv = a.w_sorted[j];
+                const int code = ofs[c];
+                sx[t] = p.x + (double)((code & 0xff) - a.R);
+                sy[t] = p.y + (double)(((code >> 8) & 0xff) - a.R);
+                sz[t] = p.z + (double)((code >> 16) - a.R);
+                swx[t] = wv.x; swy[t] = wv.y; swz[t] = wv.z;
+                sm[t] = p.w;
+            }
+            __syncwarp();
+            for (int j = sp; j < cntT; j += S) {
+                const double dx = sx[j] - xi, dy = sy[j] - yi, dz = sz[j] - zi;
+                const double s = dx * dx + dy * dy + dz * dz + B.eps2_d;
+                const double r3 = 1.0 / (s * sqrt(s));
+                const double r5 = r3 / s;
+                const double ux = mk * swx[j] - sm[j] * wxk;
+                const double uy = mk * swy[j] - sm[j] * wyk;
+                const double uz = mk * swz[j] - sm[j] * wzk;
+                const double du = dx * ux + dy * uy + dz * uz;
+                gx += r3 * ux - 3.0 * r5 * du * dx;
+                gy += r3 * uy - 3.0 * r5 * du * dy;
+                gz += r3 * uz - 3.0 * r5 * du * dz;
+            }
+            __syncwarp();
+        }
+        for (int o = 1; o < S; o <<= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        }
+        if (sp == 0 && g < w.n) {
+            const int i = a.perm[w.first + g];
+            float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+            const double sc = B.inv_h3_d;
+            o[0] = (float)(gx * sc); o[1] = (float)(gy * sc); o[2] = (float)(gz * sc);
+        }
+    }
+}
+
+// Sorted copy of the VJP cotangent: w_sorted[k] = w[perm[k]].
+__global__ void k_gather_w(const float *__restrict__ w, int64_t n, const int *__restrict__ perm,
+                           float4 *__restrict__ ws) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        ws[k] = make_float4(w[3 * i], w[3 * i + 1], w[3 * i + 2], 0.f);
+    }
+}
+
+// a10: FP64 momentum diagnostic, P = sum_i m_i a_i and sum_i m_i |a_i|,
+// two-level fixed-order reduction (deterministic).
+__global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sorted,
+                                                  const int *__restrict__ perm, const void *acc,
+                                                  int f64, int64_t n, double *partial) {
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        const double m = sorted[k].w;
+        double v[3];
+        if (f64) {
+            const double *p = reinterpret_cast<const double *>(acc) + 3 * i;
+            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
+        } else {
+            const float *p = reinterpret_cast<const float *>(acc) + 3 * i;
+            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
+        }
+        s[0] += m * v[0];
+        s[1] += m * v[1];
+        s[2] += m * v[2];
+        s[3] += m * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    }
+    __shared__ double red[8][4];
+    for (int c = 0; c < 4; ++c) {
+        double x = s[c];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double x = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][threadIdx.x];
+        partial[4 * blockIdx.x + threadIdx.x] = x;
+    }
+}
+
+__global__ void k_momentum_final(const double *partial, int nb, double *out) {
+    if (threadIdx.x < 4) {
+        double x = 0;
+        for (int b = 0; b < nb; ++b) x += partial[4 * b + threadIdx.x];
+        out[threadIdx.x] = x;
+    }
+}
+
+template <typename F>
+void *fptr(F f) { return reinterpret_cast<void *>(f); }
+
+void *pair_kernel(int prec, int K, int eq) {
+    if (prec == NF_PREC_FP64_REF) return fptr(k_pairs_f64);
+    const bool comp = prec == NF_PREC_FP32_COMP;
+#define NF_SEL(KK)                                                                       \
+    if (K == KK) {                                                                       \
+        if (eq) return comp ? fptr(k_pairs<KK, true, true>) : fptr(k_pairs<KK, true, false>); \
+        return comp ? fptr(k_pairs<KK, false, true>) : fptr(k_pairs<KK, false, false>);  \
+    }
+    NF_SEL(1)
+    NF_SEL(2)
+    NF_SEL(4)
+#undef NF_SEL
+    return nullptr;
+}
+
+void *vjp_kernel(int prec, int K, int eq) {
+    if (prec == NF_PREC_FP64_REF) return fptr(k_vjp_f64);
+    if (K == 1) return eq ? fptr(k_vjp<1, true>) : fptr(k_vjp<1, false>);
+    if (K == 2) return eq ? fptr(k_vjp<2, true>) : fptr(k_vjp<2, false>);
+    if (K == 4) return eq ? fptr(k_vjp<4, true>) : fptr(k_vjp<4, false>);
+    return nullptr;
+}
+
+int table_stride(int R) {
+    const int nbr = (2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    return (nbr + 1 + 3) & ~3;
+}
+
+size_t smem_per_warp(int prec, int R, int eq, int vjp) {
+    const int tbl = table_stride(R);
+    if (prec == NF_PREC_FP64_REF) {
+        const int nf = vjp ? 7 : 4;
+        return sizeof(double) * (size_t)(nf * kTile + (3 * tbl + 1) / 2);
+    }
+    const int nf = vjp ? (eq ? 6 : 7) : (eq ? 3 : 4);
+    return sizeof(float) * (size_t)(nf * kTile + 3 * tbl);
+}
+
+cudaError_t prepare(void *fn, size_t smem) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_generic(Ctx *c, void *fn, int vjp, const PairArgs &args, const nf_tuning &t,
+                           cudaStream_t s) {
+    const int warps = t.warps_per_block;
+    const size_t smem = smem_per_warp(c->precision, c->R, c->equal_mass, vjp) * warps;
+    cudaError_t e = prepare(fn, smem);
+    if (e) return e;
+    int per_sm = t.blocks_per_sm;
+    if (per_sm <= 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem);
+        if (e) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int grid = c->sm_count * per_sm;
+    void *params[] = {const_cast<PairArgs *>(&args)};
+    c->launches += 1;
+    return cudaLaunchKernel(fn, dim3(grid), dim3(warps * 32), params, smem, s);
+}
+
+PairArgs make_args(Ctx *c, void *out, int out_f64) {
+    PairArgs a;
+    a.sorted = c->sorted;
+    a.sorted_d = c->sorted_d;
+    a.w_sorted = c->w_sorted;
+    a.cell_start = c->cell_start;
+    a.perm = c->perm;
+    a.boxes = c->boxes_d;
+    a.items = c->items;
+    a.st = c->state;
+    a.out = out;
+    a.out_f64 = out_f64;
+    a.R = c->R;
+    a.nbr = (2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
+    a.tbl = table_stride(c->R);
+    a.m0 = c->m0;
+    return a;
+}
+
+}  // namespace
+
+// Remainder decomposition: for r sinks left over after full items of 32K,
+// pick items (count, S) minimising the modelled warp time
+// sum_items n_src * (22 K / S + 1.5), the two terms being pair arithmetic
+// per lane and per-source staging/loop overhead.
+void make_decomp(int K, Decomp *d) {
+    const int full = 32 * K;
+    double best[129];
+    int choice[129];
+    best[0] = 0;
+    choice[0] = -1;
+    for (int r = 1; r < full; ++r) {
+        best[r] = 1e30;
+        choice[r] = 0;
+        for (int l = 0; l <= 5; ++l) {
+            const int slots = full >> l;
+            if (slots < 1) continue;
+            const double cost = 22.0 * K / (1 << l) + 1.5;
+            const double tot = slots >= r ? cost : cost + best[r - slots];
+            if (tot < best[r] - 1e-12) {
+                best[r] = tot;
+                choice[r] = l;
+            }
+        }
+    }
+    for (int r = 0; r < 128; ++r) {
+        d->n_entries[r] = 0;
+        if (r == 0 || r >= full) continue;
+        int left = r;
+        while (left > 0) {
+            int l = choice[left];
+            if (d->n_entries[r] == kDecompMax - 1)   // last slot: cover the rest
+                for (l = 5; l > 0 && (full >> l) < left; --l) {}
+            const int slots = full >> l;
+            const int take = slots >= left ? left : slots;
+            d->entry[r][d->n_entries[r]++] = (take << 8) | l;
+            left -= take;
+        }
+    }
+}
+
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
+    cudaError_t e;
+    // reset counters (everything but the error word)
+    if ((e = cudaMemsetAsync(&c->state->n_items, 0, sizeof(DevState) - sizeof(int), s))) return e;
+    WLArgs a;
+    a.boxes = c->boxes_d;
+    a.n_boxes = c->n_boxes;
+    a.R = c->R;
+    a.K = c->decomp_k;
+    a.n_cells = c->n_cells;
+    a.count = c->count;
+    a.cell_start = c->cell_start;
+    a.nsrc_cell = c->nsrc_cell;
+    a.decomp = c->decomp_d;
+    a.st = c->state;
+    a.items = c->items;
+    const unsigned blocks = (unsigned)((c->n_cells + 255) / 256);
+    k_wl_count<<<blocks, 256, 0, s>>>(a);
+    k_wl_scan<<<1, 32, 0, s>>>(c->state);
+    k_wl_write<<<blocks, 256, 0, s>>>(a);
+    c->launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s) {
+    const int K = c->precision == NF_PREC_FP64_REF ? 1 : t.sinks_per_lane;
+    void *fn = pair_kernel(c->precision, K, c->equal_mass);
+    if (!fn) return cudaErrorInvalidValue;
+    return launch_generic(c, fn, 0, make_args(c, acc, out_f64), t, s);
+}
+
+cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s) {
+    if (c->n > 0) {
+        const int64_t n = c->n;
+        int grid = (int)((n + 255) / 256);
+        if (grid > c->sm_count * 8) grid = c->sm_count * 8;
+        k_gather_w<<<grid, 256, 0, s>>>(w, n, c->perm, c->w_sorted);
+        c->launches += 1;
+        cudaError_t e = cudaGetLastError();
+        if (e) return e;
+    }
+    const int K = c->precision == NF_PREC_FP64_REF ? 1 : t.sinks_per_lane;
+    void *fn = vjp_kernel(c->precision, K, c->equal_mass);
+    if (!fn) return cudaErrorInvalidValue;
+    return launch_generic(c, fn, 1, make_args(c, grad, 0), t, s);
+}
+
+cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s) {
+    k_momentum<<<kMomBlocks, 256, 0, s>>>(c->sorted, c->perm, acc, acc_f64, c->n, c->mom_partial);
+    k_momentum_final<<<1, 32, 0, s>>>(c->mom_partial, kMomBlocks, c->mom_result);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace nf

@@ -1,0 +1,404 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances. Forces: median fractional error <= 1e-6 and 99.9th percentile
+<= 1e-4 per sink, e_i = |a_i - a_i^ref| / |a_i^ref|. Binning (cell table,
+permutation, cell-relative float32 coordinates): bit-exact. The FP64
+reference kernel: within 1e-11 of the oracle (both are double sums of the
+same pairs; they differ in summation order and in the oracle's use of
+absolute instead of cell-relative coordinates).
+
+Paper: Maksimova et al. 2021, Sec. 3.1 (cells, near field), Sec. 5.2
+(Plummer softening).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+MED_TOL, P999_TOL = 1e-6, 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2110_11398_gb300 import build
+    build.build()
+    oracle.build()
+    return torch.device("cuda", 0)
+
+
+def frac_err(got, ref):
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    den = np.linalg.norm(ref, axis=1)
+    den = np.where(den > 0, den, 1.0)
+    return np.linalg.norm(got - ref, axis=1) / den
+
+
+def assert_parity(got, ref, med=MED_TOL, p999=P999_TOL, what=""):
+    e = frac_err(got, ref)
+    m, q = float(np.median(e)), float(np.quantile(e, 0.999))
+    assert m <= med and q <= p999, f"{what}: median {m:.3e} (<= {med}), p99.9 {q:.3e} (<= {p999})"
+    return m, q
+
+
+def make_nf(box, dev, precision="fp32", capacity=None, **tune):
+    from paper_2110_11398_gb300 import NearField
+    nf = NearField(box.L, box.cpd, box.eps, radius=box.R, precision=precision,
+                   capacity=capacity or max(box.n, 1), device=dev)
+    if tune:
+        nf.set_tuning(**tune)
+    return nf
+
+
+def gpu_accel(box, dev, precision="fp32", mass=None, f64=False, **tune):
+    nf = make_nf(box, dev, precision, **tune)
+    pos = torch.from_numpy(box.pos).to(dev)
+    m = None if mass is None else torch.from_numpy(np.asarray(mass, np.float32)).to(dev)
+    nf.bin(pos, m, gm=None if m is not None else box.gm)
+    a = nf.accel(dtype=torch.float64 if f64 else torch.float32)
+    torch.cuda.synchronize()
+    out = a.cpu().numpy()
+    st = nf.stats()
+    nf.close()
+    return out, st
+
+
+# ---------------------------------------------------------------- binning
+def _bin_case(box, dev):
+    nf = make_nf(box, dev)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    cs, perm, srt = (t.cpu().numpy() for t in nf.binning())
+    nf.close()
+    ref = oracle.bin_particles(box.pos, box.L, box.cpd)
+    assert np.array_equal(cs.astype(np.int64), ref["cell_start"])
+    assert np.array_equal(perm.astype(np.int64), ref["perm"])
+    assert np.array_equal(srt[:, :3].view(np.uint32), ref["rel"].view(np.uint32))
+    assert np.all(srt[:, 3] == np.float32(box.gm))
+
+
+def test_binning_bit_exact_tiny(dev):
+    _bin_case(synth.tiny(), dev)
+
+
+@pytest.mark.parametrize("L,cpd", [(1.0, 9), (3.7, 7), (250.0, 16), (1.0, 33)])
+def test_binning_bit_exact_faces_and_non_pow2_box(dev, L, cpd):
+    rng = np.random.default_rng(cpd)
+    x = rng.random((20000, 3)).astype(np.float32) * np.float32(L)
+    faces = np.array([k * L / cpd for k in range(cpd)], np.float32)
+    near = np.concatenate([faces, np.nextafter(faces, np.float32(0)), np.nextafter(faces, np.float32(2 * L)),
+                           [np.nextafter(np.float32(L), np.float32(0))]])
+    near = near[(near >= 0) & (near < np.float32(L))]
+    blk = np.stack([near, near[::-1], np.roll(near, 5)], 1).astype(np.float32)
+    pos = np.concatenate([x, blk, x[:500]], 0)          # duplicates: stability
+    rng.shuffle(pos)
+    box = synth.Box("faces", np.ascontiguousarray(pos), L, cpd, 0.01 * L / cpd, 1.0 / len(pos))
+    _bin_case(box, dev)
+
+
+def test_binning_clustered_bit_exact(dev):
+    pos, _ = synth.clustered_box(64 ** 3, 77, n_halos=30)
+    box = synth.Box("clustered64", pos, 1.0, 17, (1 / 64) / 40, 1 / 64 ** 3)
+    _bin_case(box, dev)
+
+
+# ---------------------------------------------------------------- forward
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+def test_tiny_forward_parity(dev, precision):
+    box = synth.tiny()
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    got, st = gpu_accel(box, dev, precision)
+    assert_parity(got, ref, what=precision)
+    cid = oracle.bin_particles(box.pos, box.L, box.cpd)["cid"]
+    assert st["interactions"] == oracle.interactions(cid, box.cpd, box.R)
+    assert st["max_occupancy"] == np.bincount(cid).max()
+
+
+def test_tiny_forward_fp64_reference_kernel(dev):
+    box = synth.tiny()
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    got, _ = gpu_accel(box, dev, "fp64", f64=True)
+    e = frac_err(got, ref)
+    assert np.max(e) < 1e-11, np.max(e)
+
+
+def test_comp_is_not_less_accurate(dev):
+    box = synth.early(n_side=48, cpd=13)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    e32 = frac_err(gpu_accel(box, dev, "fp32")[0], ref)
+    ec = frac_err(gpu_accel(box, dev, "fp32_comp")[0], ref)
+    assert np.median(ec) <= np.median(e32) * 1.05
+    assert_parity(gpu_accel(box, dev, "fp32")[0], ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp", "fp64"])
+def test_unequal_masses(dev, precision):
+    box = synth.tiny(seed=5)
+    mass = np.random.default_rng(3).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    got, st = gpu_accel(box, dev, precision, mass=mass, f64=precision == "fp64")
+    if precision == "fp64":
+        assert np.max(frac_err(got, ref)) < 1e-11
+    else:
+        assert_parity(got, ref, what=precision)
+    P = np.array(st["momentum"])
+    assert np.all(np.abs(P) <= 1e-5 * st["abs_momentum"])
+
+
+@pytest.mark.parametrize("K,warps", [(1, 2), (1, 4), (2, 4), (2, 8), (4, 4), (4, 16), (2, 16)])
+def test_launch_shapes_all_agree(dev, K, warps):
+    box = synth.tiny(seed=2)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    got, _ = gpu_accel(box, dev, "fp32", sinks_per_lane=K, warps_per_block=warps)
+    assert_parity(got, ref, what=f"K={K} warps={warps}")
+
+
+@pytest.mark.parametrize("R,cpd,n", [(1, 3, 3000), (1, 8, 20000), (2, 5, 4000), (3, 7, 8000), (3, 11, 30000)])
+def test_radius_and_smallest_cpd(dev, R, cpd, n):
+    rng = np.random.default_rng(R * 100 + cpd)
+    pos = rng.random((n, 3)).astype(np.float32)
+    box = synth.Box("r", pos, 1.0, cpd, 0.05 / cpd, 1.0 / n, R)
+    ref = oracle.accel(pos, 1.0, cpd, R, box.eps, m0=box.gm)
+    got, st = gpu_accel(box, dev)
+    assert_parity(got, ref, what=f"R={R} cpd={cpd}")
+    cid = oracle.bin_particles(pos, 1.0, cpd)["cid"]
+    assert st["interactions"] == oracle.interactions(cid, cpd, R)
+
+
+def test_non_pow2_box_side(dev):
+    rng = np.random.default_rng(8)
+    L = 3.7
+    pos = (rng.random((30000, 3)) * L).astype(np.float32)
+    pos[pos >= np.float32(L)] = 0
+    box = synth.Box("L3.7", pos, L, 9, 0.02 * L / 9, 1.0 / 30000)
+    ref = oracle.accel(pos, L, 9, 2, box.eps, m0=box.gm)
+    got, _ = gpu_accel(box, dev)
+    assert_parity(got, ref)
+
+
+def test_one_dense_cell_and_empty_cells(dev):
+    """5000 particles in one cell of a CPD=9 box, plus a few elsewhere: the
+    dense cell is split over many items; most cells are empty."""
+    rng = np.random.default_rng(4)
+    dense = (np.array([4, 4, 4]) + rng.random((5000, 3))) / 9
+    sparse = rng.random((37, 3))
+    pos = np.concatenate([dense, sparse]).astype(np.float32)
+    box = synth.Box("dense", pos, 1.0, 9, 0.002, 1.0 / len(pos))
+    ref = oracle.accel(pos, 1.0, 9, 2, box.eps, m0=box.gm)
+    got, st = gpu_accel(box, dev)
+    assert_parity(got, ref)
+    assert st["max_occupancy"] >= 5000
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 33, 64, 65, 129])
+def test_tiny_sizes(dev, n):
+    rng = np.random.default_rng(n)
+    pos = rng.random((n, 3)).astype(np.float32)
+    box = synth.Box("n", pos, 1.0, 5, 0.01, 1.0)
+    got, st = gpu_accel(box, dev)
+    assert got.shape == (n, 3)
+    if n:
+        ref = oracle.accel(pos, 1.0, 5, 2, 0.01, m0=1.0)
+        if n == 1:
+            assert np.all(got == 0)
+        else:
+            assert_parity(got, ref, what=f"n={n}")
+    assert st["interactions"] == n * n          # CPD = 2R+1: every pair once
+
+
+def test_out_of_range_position_is_rejected(dev):
+    from paper_2110_11398_gb300 import NFError
+    box = synth.tiny()
+    nf = make_nf(box, dev)
+    for bad in (np.nan, 1.0, -0.25, np.inf):
+        pos = box.pos.copy()
+        pos[123, 2] = bad
+        with pytest.raises(NFError, match="NF_ERANGE"):
+            nf.bin(torch.from_numpy(pos).to(dev), gm=box.gm)
+        with pytest.raises(NFError, match="NF_ESTATE"):
+            nf.accel()
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)   # recovers
+    nf.accel()
+    nf.close()
+
+
+def test_compute_before_bin_is_an_error(dev):
+    from paper_2110_11398_gb300 import NFError
+    nf = make_nf(synth.tiny(), dev)
+    with pytest.raises(NFError, match="NF_ESTATE"):
+        nf.accel(out=torch.empty((0, 3), device=dev))
+    nf.close()
+
+
+def test_deterministic_and_graph_equals_direct(dev):
+    box = synth.tiny(seed=9)
+    a1, _ = gpu_accel(box, dev, use_graph=1)
+    a2, _ = gpu_accel(box, dev, use_graph=1)
+    a3, _ = gpu_accel(box, dev, use_graph=0)
+    assert np.array_equal(a1.view(np.uint32), a2.view(np.uint32))
+    assert np.array_equal(a1.view(np.uint32), a3.view(np.uint32))
+
+
+def test_repeated_calls_with_new_outputs_and_rebin(dev):
+    """Graph replays with changing output pointers and fresh binnings."""
+    nf = make_nf(synth.tiny(), dev)
+    outs = []
+    for seed in (0, 1, 0):
+        box = synth.tiny(seed=seed)
+        nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+        for _ in range(2):
+            outs.append(nf.accel().cpu().numpy())
+    nf.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[4])
+    assert not np.array_equal(outs[0], outs[2])
+
+
+def test_host_buffer_path_matches_device_path(dev):
+    box = synth.tiny(seed=3)
+    nf = make_nf(box, dev)
+    a_host = nf.accel_host(box.pos, gm=box.gm)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    a_dev = nf.accel().cpu().numpy()
+    nf.close()
+    assert np.array_equal(a_host, a_dev)
+
+
+def test_batched_boxes_bit_identical_to_plain(dev):
+    from paper_2110_11398_gb300 import NearField
+    boxes = synth.batched(n_boxes=4, lo_side=20, hi_side=40)
+    boxes[1].L = 2.0
+    boxes[1].pos = (boxes[1].pos * 2).astype(np.float32)
+    boxes[1].eps *= 2
+    n = sum(b.n for b in boxes)
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    nfb = NearField([b.L for b in boxes], [b.cpd for b in boxes], [b.eps for b in boxes],
+                    capacity=n, device=dev)
+    pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+    mass = torch.from_numpy(np.concatenate([np.full(b.n, b.gm, np.float32) for b in boxes])).to(dev)
+    nfb.bin(pos, mass, box_offsets=offs)
+    ab = nfb.accel().cpu().numpy()
+    inter = nfb.stats()["interactions"]
+    nfb.close()
+    tot = 0
+    for b, o0, o1 in zip(boxes, offs[:-1], offs[1:]):
+        nf = make_nf(b, dev)
+        nf.bin(torch.from_numpy(b.pos).to(dev), mass[o0:o1].contiguous())
+        ap = nf.accel().cpu().numpy()
+        tot += nf.stats()["interactions"]
+        nf.close()
+        assert np.array_equal(ab[o0:o1].view(np.uint32), ap.view(np.uint32))
+        ref = oracle.accel(b.pos, b.L, b.cpd, b.R, b.eps, m0=b.gm,
+                           sinks=np.arange(0, b.n, 7))
+        assert_parity(ap[::7], ref, what=b.name)
+    assert inter == tot
+
+
+def test_autotune_picks_a_valid_shape(dev):
+    box = synth.tiny()
+    nf = make_nf(box, dev)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    t = nf.autotune(reps=1)
+    assert t["sinks_per_lane"] in (1, 2, 4) and t["warps_per_block"] in (4, 8)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    assert_parity(nf.accel().cpu().numpy(), ref)
+    nf.close()
+
+
+def test_momentum_diagnostic(dev):
+    box = synth.tiny()
+    _, st = gpu_accel(box, dev)
+    P = np.array(st["momentum"])
+    assert st["abs_momentum"] > 0
+    assert np.all(np.abs(P) <= 1e-5 * st["abs_momentum"]), (P, st["abs_momentum"])
+
+
+# ---------------------------------------------------------------- adjoint
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_tiny_vjp_parity(dev, precision):
+    box = synth.tiny()
+    w = synth.cotangent(box.n, 4)
+    ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    nf = make_nf(box, dev, precision)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    g = nf.vjp(torch.from_numpy(w).to(dev)).cpu().numpy()
+    nf.close()
+    if precision == "fp64":
+        assert np.median(frac_err(g, ref)) < 1e-7    # FP64 pairs, FP32 output
+    else:
+        assert_parity(g, ref, what="vjp")
+
+
+def test_vjp_unequal_masses(dev):
+    box = synth.tiny(seed=6)
+    mass = np.random.default_rng(1).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    w = synth.cotangent(box.n, 5)
+    ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    nf = make_nf(box, dev)
+    nf.bin(torch.from_numpy(box.pos).to(dev), torch.from_numpy(mass).to(dev))
+    g = nf.vjp(torch.from_numpy(w).to(dev)).cpu().numpy()
+    nf.close()
+    assert_parity(g, ref, what="vjp masses")
+    assert np.abs(g.astype(np.float64).sum(0)).max() <= 1e-5 * np.abs(g).sum()
+
+
+def test_autograd_matches_vjp(dev):
+    from paper_2110_11398_gb300 import accel
+    box = synth.tiny(seed=1)
+    nf = make_nf(box, dev)
+    p = torch.from_numpy(box.pos).to(dev).requires_grad_(True)
+    a = accel(p, nf, gm=box.gm)
+    w = torch.from_numpy(synth.cotangent(box.n, 2)).to(dev)
+    (g,) = torch.autograd.grad(a, p, grad_outputs=w)
+    g2 = nf.vjp(w)
+    assert torch.equal(g, g2)
+    nf.close()
+
+
+# ---------------------------------------------------------------- full sizes
+def _sampled(box, dev, n_sample, seed, precision="fp32", w=None):
+    from paper_2110_11398_gb300 import NearField
+    nf = NearField(box.L, box.cpd, box.eps, radius=box.R, precision=precision, capacity=box.n, device=dev)
+    pos = torch.from_numpy(box.pos).to(dev)
+    nf.bin(pos, gm=box.gm)
+    if w is None:
+        out = nf.accel()
+    else:
+        out = nf.vjp(torch.from_numpy(w).to(dev))
+    st = nf.stats()
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(box.n, n_sample, replace=False))
+    got = out[torch.from_numpy(idx).to(dev)].cpu().numpy()
+    nf.close()
+    del pos, out
+    torch.cuda.empty_cache()
+    return idx, got, st
+
+
+def test_early_full_size_sampled(dev):
+    box = synth.early()
+    idx, got, st = _sampled(box, dev, 20000, 11)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
+    m, q = assert_parity(got, ref, what="early 256^3")
+    P = np.array(st["momentum"])
+    assert np.all(np.abs(P) <= 1e-5 * st["abs_momentum"])
+
+
+def test_late_full_size_sampled(dev):
+    box = synth.late()
+    idx, got, st = _sampled(box, dev, 2000, 12)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
+    assert_parity(got, ref, what="late 512^3")
+    assert st["max_occupancy"] > 10000
+
+
+def test_adjoint_full_size_sampled(dev):
+    box = synth.adjoint()
+    w = synth.cotangent(box.n, box.seed)
+    idx, got, _ = _sampled(box, dev, 5000, 13, w=w)
+    ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
+    assert_parity(got, ref, what="adjoint 128^3")
