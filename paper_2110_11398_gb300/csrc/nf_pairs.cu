@@ -338,6 +338,12 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             const f2_t *py = reinterpret_cast<const f2_t *>(sy);
             const f2_t *pz = reinterpret_cast<const f2_t *>(sz);
             const f2_t *pm = reinterpret_cast<const f2_t *>(sm);
+            // per-tile partial sums (plain FP32): each tile's <= 64/S terms per
+            // accumulator are summed afresh and then folded into the running
+            // total, which keeps the rounding random walk short
+            f2_t tx[K], ty[K], tz[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
 #pragma unroll 2
             for (int pp = sp; pp < npair; pp += S) {
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
@@ -355,15 +361,23 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     f2_t f = f2_mul(f2_mul(r, r), r);
                     if (!EQ) f = f2_mul(f, m2);
                     if (!COMP) {
-                        ax[k] = f2_fma(f, dx, ax[k]);
-                        ay[k] = f2_fma(f, dy, ay[k]);
-                        az[k] = f2_fma(f, dz, az[k]);
+                        tx[k] = f2_fma(f, dx, tx[k]);
+                        ty[k] = f2_fma(f, dy, ty[k]);
+                        tz[k] = f2_fma(f, dz, tz[k]);
                     } else {
                         f2_t e;
                         two_sum(ax[k], f2_mul(f, dx), ax[k], e); lx[k] = f2_add(lx[k], e);
                         two_sum(ay[k], f2_mul(f, dy), ay[k], e); ly[k] = f2_add(ly[k], e);
                         two_sum(az[k], f2_mul(f, dz), az[k], e); lz[k] = f2_add(lz[k], e);
                     }
+                }
+            }
+            if (!COMP) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    ax[k] = f2_add(ax[k], tx[k]);
+                    ay[k] = f2_add(ay[k], ty[k]);
+                    az[k] = f2_add(az[k], tz[k]);
                 }
             }
             __syncwarp();
@@ -490,8 +504,11 @@ __global__ void __launch_bounds__(512) k_pairs_f64(PairArgs a) {
 }
 
 // Adjoint (vector-Jacobian product) pair kernel:
-//   g_k = sum_j J(D)(m_k w_j - m_j w_k),  J(D) u = s^-3/2 u - 3 s^-5/2 D (D.u)
-// accumulated as G1 = sum s^-3/2 u and G2 = sum s^-5/2 (D.u) D, g = G1 - 3 G2.
+//   g_k = sum_j J(D)(m_k w_j - m_j w_k),  J(D) u = s^-3/2 u - 3 s^-5/2 D (D.u).
+// Each pair's whole J u goes into one accumulator: the two parts of J u grow
+// coherently over j (the -m_j w_k term points the same way for every j) and
+// only cancel in their sum, so accumulating them apart loses precision.
+// Sums are blocked per tile like the forward kernel.
 template <int K, bool EQ>
 __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
         const f2_t eps2 = f2_pack(B.eps2, B.eps2);
 
         f2_t xi[K], yi[K], zi[K], wxi[K], wyi[K], wzi[K], mi[K];
-        f2_t g1x[K], g1y[K], g1z[K], g2x[K], g2y[K], g2z[K];
+        f2_t gx[K], gy[K], gz[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int si = g + G * k;
@@ -531,8 +548,9 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
             xi[k] = f2_pack(p.x, p.x); yi[k] = f2_pack(p.y, p.y); zi[k] = f2_pack(p.z, p.z);
             wxi[k] = f2_pack(wv.x, wv.x); wyi[k] = f2_pack(wv.y, wv.y); wzi[k] = f2_pack(wv.z, wv.z);
             mi[k] = f2_pack(p.w, p.w);
-            g1x[k] = g1y[k] = g1z[k] = g2x[k] = g2y[k] = g2z[k] = 0ull;
+            gx[k] = gy[k] = gz[k] = 0ull;
         }
+        const f2_t minus3 = f2_pack(-3.0f, -3.0f);
         int ci = 0;
         for (int q0 = 0; q0 < nsrc; q0 += kTile) {
             const int cntT = min(kTile, nsrc - q0);
@@ -564,6 +582,9 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
             const f2_t *pwy = reinterpret_cast<const f2_t *>(swy);
             const f2_t *pwz = reinterpret_cast<const f2_t *>(swz);
             const f2_t *pm = reinterpret_cast<const f2_t *>(sm);
+            f2_t tx[K], ty[K], tz[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
             for (int pp = sp; pp < npair; pp += S) {
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
                 const f2_t wx2 = pwx[pp], wy2 = pwy[pp], wz2 = pwz[pp];
@@ -587,41 +608,43 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
                         uy = f2_sub(wy2, wyi[k]);
                         uz = f2_sub(wz2, wzi[k]);
                     } else {
-                        // m_k w_j - m_j w_k
-                        ux = f2_sub(f2_mul(mi[k], wx2), f2_mul(m2, wxi[k]));
-                        uy = f2_sub(f2_mul(mi[k], wy2), f2_mul(m2, wyi[k]));
-                        uz = f2_sub(f2_mul(mi[k], wz2), f2_mul(m2, wzi[k]));
+                        // m_k w_j - m_j w_k written as m_k (w_j - w_k) + (m_k - m_j) w_k:
+                        // for the self pair every factor is an exact zero, so u
+                        // stays 0 even if the compiler fuses a product into an
+                        // FMA (the self pair carries the large weight eps^-3)
+                        const f2_t dm = f2_sub(mi[k], m2);
+                        ux = f2_fma(mi[k], f2_sub(wx2, wxi[k]), f2_mul(dm, wxi[k]));
+                        uy = f2_fma(mi[k], f2_sub(wy2, wyi[k]), f2_mul(dm, wyi[k]));
+                        uz = f2_fma(mi[k], f2_sub(wz2, wzi[k]), f2_mul(dm, wzi[k]));
                     }
                     f2_t du = f2_mul(dx, ux);
                     du = f2_fma(dy, uy, du);
                     du = f2_fma(dz, uz, du);
-                    const f2_t c = f2_mul(du, r5);
-                    g1x[k] = f2_fma(r3, ux, g1x[k]);
-                    g1y[k] = f2_fma(r3, uy, g1y[k]);
-                    g1z[k] = f2_fma(r3, uz, g1z[k]);
-                    g2x[k] = f2_fma(c, dx, g2x[k]);
-                    g2y[k] = f2_fma(c, dy, g2y[k]);
-                    g2z[k] = f2_fma(c, dz, g2z[k]);
+                    const f2_t c = f2_mul(f2_mul(du, r5), minus3);
+                    tx[k] = f2_fma(c, dx, f2_fma(r3, ux, tx[k]));
+                    ty[k] = f2_fma(c, dy, f2_fma(r3, uy, ty[k]));
+                    tz[k] = f2_fma(c, dz, f2_fma(r3, uz, tz[k]));
                 }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                gx[k] = f2_add(gx[k], tx[k]);
+                gy[k] = f2_add(gy[k], ty[k]);
+                gz[k] = f2_add(gz[k], tz[k]);
             }
             __syncwarp();
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            const f2_t g1[3] = {g1x[k], g1y[k], g1z[k]};
-            const f2_t g2[3] = {g2x[k], g2y[k], g2z[k]};
+            const f2_t gg[3] = {gx[k], gy[k], gz[k]};
             float v[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float a0, a1, b0, b1;
-                f2_unpack(g1[c], a0, a1);
-                f2_unpack(g2[c], b0, b1);
-                float s1 = a0 + a1, s2 = b0 + b1;
-                for (int o = 1; o < S; o <<= 1) {
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                }
-                v[c] = s1 - 3.0f * s2;
+                float a0, a1;
+                f2_unpack(gg[c], a0, a1);
+                float s1 = a0 + a1;
+                for (int o = 1; o < S; o <<= 1) s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                v[c] = s1;
             }
             const int si = g + G * k;
             if (sp == 0 && si < w.n) {
@@ -689,9 +712,11 @@ __global__ void __launch_bounds__(512) k_vjp_f64(PairArgs a) {
                 const double s = dx * dx + dy * dy + dz * dz + B.eps2_d;
                 const double r3 = 1.0 / (s * sqrt(s));
                 const double r5 = r3 / s;
-                const double ux = mk * swx[j] - sm[j] * wxk;
-                const double uy = mk * swy[j] - sm[j] * wyk;
-                const double uz = mk * swz[j] - sm[j] * wzk;
+                // m_k w_j - m_j w_k, exactly 0 for the self pair (see k_vjp)
+                const double dm = mk - sm[j];
+                const double ux = mk * (swx[j] - wxk) + dm * wxk;
+                const double uy = mk * (swy[j] - wyk) + dm * wyk;
+                const double uz = mk * (swz[j] - wzk) + dm * wzk;
                 const double du = dx * ux + dy * uy + dz * uz;
                 gx += r3 * ux - 3.0 * r5 * du * dx;
                 gy += r3 * uy - 3.0 * r5 * du * dy;
