@@ -46,6 +46,30 @@ def dist_env():
     return rank, world, local
 
 
+def shard(n_items: int, rank: int, world: int) -> range:
+    """Contiguous share of n_items for one rank (boxes of the batched workload)."""
+    base, extra = divmod(n_items, world)
+    start = rank * base + min(rank, extra)
+    return range(start, start + base + (1 if rank < extra else 0))
+
+
+def aggregate(local_ms: float, local_units: float, dist=None) -> tuple[float, float]:
+    """(max over ranks of the timed region in ms, sum over ranks of the units).
+
+    value = units / (max_ms / 1e3): the whole job is as slow as its slowest rank.
+    """
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(local_ms), float(local_units)
+    import torch
+    backend = dist.get_backend()
+    dev = torch.device("cuda", torch.cuda.current_device()) if backend == "nccl" else torch.device("cpu")
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -130,11 +154,16 @@ def oracle_sample(box, target_s: float, seed: int = 123):
     rng = np.random.default_rng(seed)
     order = rng.permutation(box.n)
     pos64 = box.pos.astype(np.float64)
-    # calibrate on a small sample
-    k = min(box.n, 256)
-    t0 = time.perf_counter()
-    oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=order[:k], cid=b["cid"])
-    dt = max(time.perf_counter() - t0, 1e-4)
+    # calibrate: grow a sample until it takes a measurable share of the target
+    # (small samples under-use the OpenMP threads and under-estimate the rate)
+    k = min(box.n, 1024)
+    while True:
+        t0 = time.perf_counter()
+        oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=order[:k], cid=b["cid"])
+        dt = max(time.perf_counter() - t0, 1e-4)
+        if dt >= 0.1 * target_s or k >= box.n:
+            break
+        k = min(box.n, k * 4)
     rate = nsrc[order[:k]].sum() / dt
     # grow the sample until it holds ~target_s of work at that rate
     cum = np.cumsum(nsrc[order])
@@ -161,11 +190,16 @@ def run_reference(args):
     pos64 = box.pos.astype(np.float64)
     rng = np.random.default_rng(7)
     order = rng.permutation(box.n)
-    k = min(box.n, 256)
-    t0 = time.perf_counter()
-    oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=order[:k], cid=b["cid"])
-    rate = nsrc[order[:k]].sum() / max(time.perf_counter() - t0, 1e-4)
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    k = min(box.n, 1024)
+    while True:
+        t0 = time.perf_counter()
+        oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=order[:k], cid=b["cid"])
+        dt = max(time.perf_counter() - t0, 1e-4)
+        if dt >= 0.1 * per_step or k >= box.n:
+            break
+        k = min(box.n, k * 4)
+    rate = nsrc[order[:k]].sum() / dt
     cum = np.cumsum(nsrc[order])
     m = max(k, min(box.n, int(np.searchsorted(cum, rate * per_step)) + 1))
     tot_inter, tot_t = 0, 0.0
@@ -251,12 +285,9 @@ def run_ours(args):
     clk = clocks.stop()
     elapsed_ms = e0.elapsed_time(e1)
     launches = nf.stats()["kernel_launches"] - launches0
-    t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, units = aggregate(elapsed_ms, interactions * args.steps, dist if world > 1 else None)
     ms_per_step = ms_max / args.steps
-    value = world * interactions * args.steps / (ms_max / 1e3)
+    value = units / (ms_max / 1e3)
     updates = world * n * args.steps / (ms_max / 1e3)
 
     # roofline of the dominant kernel (the pair kernel), from its live duration

@@ -108,13 +108,14 @@ int ensure_decomp(Ctx *c, int K, cudaStream_t s) {
 }
 
 // The compute phase: work list, pair kernel, momentum diagnostic and the
-// copy of the counters to pinned host memory.
+// copy of the counters to pinned host memory. The pair kernel is bracketed by
+// "external" event records, which stay real records inside a captured graph.
 cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
-    if ((e = cudaEventRecord(c->ev_pair0, s))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev_pair0, s, cudaEventRecordExternal))) return e;
     if ((e = nf::launch_pairs(c, acc, f64, c->tune, s))) return e;
-    if ((e = cudaEventRecord(c->ev_pair1, s))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev_pair1, s, cudaEventRecordExternal))) return e;
     if ((e = nf::launch_momentum(c, acc, f64, s))) return e;
     if ((e = cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s)))
         return e;
@@ -124,9 +125,9 @@ cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
 cudaError_t enqueue_vjp(Ctx *c, const float *w, float *grad, cudaStream_t s) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
-    if ((e = cudaEventRecord(c->ev_pair0, s))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev_pair0, s, cudaEventRecordExternal))) return e;
     if ((e = nf::launch_vjp(c, w, grad, c->tune, s))) return e;
-    if ((e = cudaEventRecord(c->ev_pair1, s))) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev_pair1, s, cudaEventRecordExternal))) return e;
     return cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s);
 }
 
