@@ -107,15 +107,25 @@ int ensure_decomp(Ctx *c, int K, cudaStream_t s) {
     return NF_OK;
 }
 
+// Event record that stays a real (timed) record when `s` is being captured
+// into a graph: there it must be an "external" record node, while a stream
+// that is not capturing takes the plain form.
+cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e) return e;
+    if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    return cudaEventRecord(ev, s);
+}
+
 // The compute phase: work list, pair kernel, momentum diagnostic and the
-// copy of the counters to pinned host memory. The pair kernel is bracketed by
-// "external" event records, which stay real records inside a captured graph.
+// copy of the counters to pinned host memory.
 cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
-    if ((e = cudaEventRecordWithFlags(c->ev_pair0, s, cudaEventRecordExternal))) return e;
+    if ((e = record_timing(c->ev_pair0, s))) return e;
     if ((e = nf::launch_pairs(c, acc, f64, c->tune, s))) return e;
-    if ((e = cudaEventRecordWithFlags(c->ev_pair1, s, cudaEventRecordExternal))) return e;
+    if ((e = record_timing(c->ev_pair1, s))) return e;
     if ((e = nf::launch_momentum(c, acc, f64, s))) return e;
     if ((e = cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s)))
         return e;
@@ -125,9 +135,9 @@ cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
 cudaError_t enqueue_vjp(Ctx *c, const float *w, float *grad, cudaStream_t s) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
-    if ((e = cudaEventRecordWithFlags(c->ev_pair0, s, cudaEventRecordExternal))) return e;
+    if ((e = record_timing(c->ev_pair0, s))) return e;
     if ((e = nf::launch_vjp(c, w, grad, c->tune, s))) return e;
-    if ((e = cudaEventRecordWithFlags(c->ev_pair1, s, cudaEventRecordExternal))) return e;
+    if ((e = record_timing(c->ev_pair1, s))) return e;
     return cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s);
 }
 
