@@ -205,8 +205,40 @@ NF_API int nf_get_tuning(const nf_ctx *ctx, nf_tuning *t);
  */
 NF_API int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream);
 
+/*
+ * nf_bin_cells_noalloc -- the binning of nf_bin_particles for one box, for
+ * callers that cannot allocate device memory: for example a host program
+ * whose own pool allocator already holds the GPU's memory (a further
+ * cudaMalloc would fail or fragment that pool), or a latency-critical loop
+ * that cannot afford cudaMalloc's implicit device-wide synchronisation. The
+ * paper has no counterpart to this call; it exists for such callers only.
+ *
+ * It allocates nothing. Its scratch (radix keys and values, cell counts,
+ * histograms, scan partials, error word) lives in one file-scope device array
+ * of about 17 MB, which every GPU that loads libnf holds until the process
+ * exits. Limits: n <= 1,048,576 particles and CPD^3 <= 262,144 cells
+ * (CPD <= 64); larger requests return NF_EINVAL.
+ *   pos          device [n x 3] float32 in [0, box_size)
+ *   mass         device [n] float32 G*m, or NULL for mass_if_null
+ *   cell_start   device [CPD^3 + 1] int32 out (as nf_copy_binning)
+ *   perm         device [n] int32 out
+ *   sorted       device [n x 4] float32 out, 16-byte aligned, records
+ *                (rx, ry, rz, G m) in cell units (as nf_copy_binning)
+ * Runs on the current CUDA device and synchronises `stream` before
+ * returning (to report NF_ERANGE). The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture. All calls on a device share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams or threads) race and must be serialised by the caller.
+ * Errors: NF_EINVAL, NF_ERANGE, NF_ECUDA; message via nf_last_error(NULL).
+ */
+NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, double mass_if_null,
+                                int64_t n, double box_size, int cpd, int32_t *cell_start,
+                                int32_t *perm, float *sorted, void *stream);
+
 /* nf_last_error -- message of the last failing call on ctx (never NULL);
- * with ctx == NULL, the message of the last failing nf_init in this thread. */
+ * with ctx == NULL, the message of the last failing nf_init or
+ * nf_bin_cells_noalloc in this thread. */
 NF_API const char *nf_last_error(const nf_ctx *ctx);
 
 /* nf_status_string -- static name of a status code. */

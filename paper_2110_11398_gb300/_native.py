@@ -20,8 +20,8 @@ PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_P
 # every entry point include/nf.h declares
 EXPORTS = ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
            "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
-           "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_last_error", "nf_status_string",
-           "nf_free")
+           "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
+           "nf_last_error", "nf_status_string", "nf_free")
 
 
 class nf_stats(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(path: str | None = None):
         lib.nf_get_tuning.argtypes = [vp, P(nf_tuning)]
         lib.nf_autotune.argtypes = [vp, i32, P(nf_tuning), vp]
         lib.nf_copy_binning.argtypes = [vp, vp, vp, vp, vp]
+        lib.nf_bin_cells_noalloc.argtypes = [vp, vp, dbl, i64, dbl, i32, vp, vp, vp, vp]
         lib.nf_last_error.argtypes = [vp]
         lib.nf_last_error.restype = ctypes.c_char_p
         lib.nf_status_string.argtypes = [i32]
@@ -86,7 +87,7 @@ def load(path: str | None = None):
         lib.nf_free.restype = None
         for name in ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
                      "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
-                     "nf_get_tuning", "nf_autotune", "nf_copy_binning"):
+                     "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

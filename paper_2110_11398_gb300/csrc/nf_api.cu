@@ -204,6 +204,11 @@ int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
 
 }  // namespace
 
+namespace nf {
+// Message of a failing call that has no context (read by nf_last_error(NULL)).
+void set_thread_error(const char *msg) { g_init_err = msg ? msg : ""; }
+}  // namespace nf
+
 extern "C" {
 
 const char *nf_status_string(int status) {

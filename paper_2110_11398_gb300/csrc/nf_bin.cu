@@ -9,6 +9,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <mutex>
+
 #include "nf_ctx.h"
 #include "nf_internal.cuh"
 
@@ -360,3 +363,163 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
 }
 
 }  // namespace nf
+
+// ---------------------------------------------------------------- no-alloc binning
+// nf_bin_cells_noalloc: the binning above for one box, with every scratch
+// buffer carved out of one file-scope device array instead of cudaMalloc.
+// It serves callers that must not allocate device memory themselves or
+// through a library, e.g. a host program whose own pool already reserves the
+// GPU's memory (a further cudaMalloc would fail or fragment it), or a
+// latency-critical loop that cannot pay cudaMalloc's implicit device-wide
+// synchronisation. The paper has no counterpart to this call.
+namespace nf {
+void set_thread_error(const char *msg);
+}
+
+namespace {
+
+constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 20;   // 1,048,576
+constexpr int64_t kNoAllocMaxCells = int64_t(1) << 18;       // CPD^3 <= 262,144
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxParticles + nf::kRadixTile - 1) / nf::kRadixTile;
+constexpr int64_t kNoAllocScanInts = 256;
+
+constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t kOffKeysA = 0;
+constexpr size_t kOffKeysB = kOffKeysA + align256(4 * kNoAllocMaxParticles);
+constexpr size_t kOffValsA = kOffKeysB + align256(4 * kNoAllocMaxParticles);
+constexpr size_t kOffValsB = kOffValsA + align256(4 * kNoAllocMaxParticles);
+constexpr size_t kOffCount = kOffValsB + align256(4 * kNoAllocMaxParticles);
+constexpr size_t kOffHist = kOffCount + align256(4 * kNoAllocMaxCells);
+constexpr size_t kOffScan = kOffHist + align256(4 * (nf::kRadixDigits * kNoAllocTiles + 1));
+constexpr size_t kOffState = kOffScan + align256(4 * kNoAllocScanInts);
+constexpr size_t kOffBox = kOffState + align256(sizeof(nf::DevState));
+constexpr size_t kOffPoff = kOffBox + align256(sizeof(nf::BoxDev));
+constexpr size_t kNoAllocBytes = kOffPoff + align256(2 * sizeof(int64_t));   // about 17.3 MB
+
+// Shared by every call on a device and kept (with the last call's contents)
+// until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[kNoAllocMaxDevices] = {};
+int g_noalloc_sms[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up
+// once per device with that device current.
+int noalloc_setup(int dev, unsigned char **base, int *sms) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return NF_ECUDA;
+        }
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return NF_ECUDA;
+        }
+        g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+        g_noalloc_sms[dev] = n;
+    }
+    *base = g_noalloc_base[dev];
+    *sms = g_noalloc_sms[dev];
+    return NF_OK;
+}
+
+}  // namespace
+
+extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, double mass_if_null,
+                                           int64_t n, double box_size, int cpd,
+                                           int32_t *cell_start, int32_t *perm, float *sorted,
+                                           void *stream) {
+    using namespace nf;
+    const int64_t ncell = (int64_t)cpd * cpd * cpd;
+    if (n < 0 || n > kNoAllocMaxParticles) {
+        set_thread_error("nf_bin_cells_noalloc: n must be in [0, 1048576]");
+        return NF_EINVAL;
+    }
+    if (cpd < 1 || ncell > kNoAllocMaxCells) {
+        set_thread_error("nf_bin_cells_noalloc: cpd must be in [1, 64] (CPD^3 <= 262144)");
+        return NF_EINVAL;
+    }
+    if (!(box_size > 0.0) || !(box_size < 1e300)) {
+        set_thread_error("nf_bin_cells_noalloc: box_size must be finite and > 0");
+        return NF_EINVAL;
+    }
+    if (!cell_start || (n > 0 && (!pos || !perm || !sorted))) {
+        set_thread_error("nf_bin_cells_noalloc: pos, cell_start, perm and sorted are required");
+        return NF_EINVAL;
+    }
+    if (reinterpret_cast<uintptr_t>(sorted) % 16 != 0) {
+        set_thread_error("nf_bin_cells_noalloc: sorted must be 16-byte aligned");
+        return NF_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+        cudaGetLastError();
+        set_thread_error("nf_bin_cells_noalloc: no usable current CUDA device");
+        return NF_ECUDA;
+    }
+    unsigned char *base = nullptr;
+    int sms = 0;
+    if (noalloc_setup(dev, &base, &sms) != NF_OK) {
+        set_thread_error("nf_bin_cells_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return NF_ECUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    // A context on the stack whose buffers are views of the static array and
+    // of the caller's outputs; the existing binning launcher runs on it.
+    Ctx c;
+    c.device = dev;
+    c.n_boxes = 1;
+    c.precision = NF_PREC_FP32;
+    c.capacity = kNoAllocMaxParticles;
+    c.n_cells = ncell;
+    c.sm_count = sms;
+    c.keys_a = reinterpret_cast<int *>(base + kOffKeysA);
+    c.keys_b = reinterpret_cast<int *>(base + kOffKeysB);
+    c.vals_a = reinterpret_cast<int *>(base + kOffValsA);
+    c.vals_b = reinterpret_cast<int *>(base + kOffValsB);
+    c.count = reinterpret_cast<int *>(base + kOffCount);
+    c.radix_hist = reinterpret_cast<int *>(base + kOffHist);
+    c.scan_tmp = reinterpret_cast<int *>(base + kOffScan);
+    c.state = reinterpret_cast<DevState *>(base + kOffState);
+    c.boxes_d = reinterpret_cast<BoxDev *>(base + kOffBox);
+    c.poff_d = reinterpret_cast<int64_t *>(base + kOffPoff);
+    c.cell_start = cell_start;
+    c.sorted = reinterpret_cast<float4 *>(sorted);
+
+    BoxDev B{};
+    const double h = box_size / cpd;
+    B.L = box_size;
+    B.cpd_d = (double)cpd;
+    B.cpd = cpd;
+    B.cell_off = 0;
+    B.inv_h2_d = 1.0 / (h * h);
+    B.inv_h3_d = 1.0 / (h * h * h);
+    int ex = 0;
+    c.pow2_all = std::frexp(box_size, &ex) == 0.5 ? 1 : 0;
+    const int64_t poff[2] = {0, n};
+    cudaError_t e = cudaMemcpyAsync(c.boxes_d, &B, sizeof(B), cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemcpyAsync(c.poff_d, poff, sizeof(poff), cudaMemcpyHostToDevice, s);
+    if (!e) e = launch_bin(&c, pos, mass, (float)mass_if_null, n, s);
+    if (!e && n > 0) e = cudaMemcpyAsync(perm, c.perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
+    int err_word = 0;
+    if (!e) e = cudaMemcpyAsync(&err_word, &c.state->error, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) {
+        cudaGetLastError();
+        set_thread_error(cudaGetErrorString(e));
+        return NF_ECUDA;
+    }
+    if (err_word) {
+        set_thread_error("nf_bin_cells_noalloc: a position component is not finite or outside [0, L)");
+        return NF_ERANGE;
+    }
+    return NF_OK;
+}
