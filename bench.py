@@ -179,47 +179,66 @@ def oracle_sample(box, target_s: float, seed: int = 123):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
-    """The oracle (FP64 C, OpenMP over sinks) as it stands, on host cores."""
+    """The oracle (FP64 C, OpenMP over sinks) as it stands, on host cores,
+    on bounded sink samples of the same workload (accelerations; the VJP for
+    the adjoint workload; the boxes in turn for the batched workload)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    box = make_workload(args.workload)
-    b = oracle.bin_particles(box.pos, box.L, box.cpd)
-    _, nsrc = oracle.interactions(b["cid"], box.cpd, box.R, per_sink=True)
-    pos64 = box.pos.astype(np.float64)
-    rng = np.random.default_rng(7)
-    order = rng.permutation(box.n)
+    import synth
+    boxes = synth.batched() if args.workload == "batched" else [make_workload(args.workload)]
+    vjp = args.workload == "adjoint"
+    prepared = []
+    for box in boxes:
+        b = oracle.bin_particles(box.pos, box.L, box.cpd)
+        _, nsrc = oracle.interactions(b["cid"], box.cpd, box.R, per_sink=True)
+        w = synth.cotangent(box.n, box.seed) if vjp else None
+        prepared.append((box, b["cid"], nsrc, box.pos.astype(np.float64), w))
+
+    def run_on(p, idx):
+        box, cid, _, pos64, w = p
+        if vjp:
+            return oracle.vjp(pos64, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, cid=cid)
+        return oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, cid=cid)
+
     per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    k = min(box.n, 1024)
-    while True:
-        t0 = time.perf_counter()
-        oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=order[:k], cid=b["cid"])
-        dt = max(time.perf_counter() - t0, 1e-4)
-        if dt >= 0.1 * per_step or k >= box.n:
-            break
-        k = min(box.n, k * 4)
-    rate = nsrc[order[:k]].sum() / dt
-    cum = np.cumsum(nsrc[order])
-    m = max(k, min(box.n, int(np.searchsorted(cum, rate * per_step)) + 1))
-    tot_inter, tot_t = 0, 0.0
+    rng = np.random.default_rng(7)
+    tot_inter, tot_t, sizes = 0, 0.0, []
     for step in range(args.warmup + args.steps):
-        idx = np.sort(order[(step * m) % box.n:][:m])
+        p = prepared[step % len(prepared)]
+        box, _, nsrc, _, _ = p
+        order = rng.permutation(box.n)
+        k = min(box.n, 1024)
+        while True:       # calibrate the sample on this box
+            t0 = time.perf_counter()
+            run_on(p, np.sort(order[:k]))
+            dt = max(time.perf_counter() - t0, 1e-4)
+            if dt >= 0.1 * per_step or k >= box.n:
+                break
+            k = min(box.n, k * 4)
+        rate = nsrc[order[:k]].sum() / dt
+        m = max(k, min(box.n, int(np.searchsorted(np.cumsum(nsrc[order]), rate * per_step)) + 1))
+        idx = np.sort(order[:m])
         t0 = time.perf_counter()
-        oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, cid=b["cid"])
+        run_on(p, idx)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             tot_inter += int(nsrc[idx].sum())
             tot_t += dt
+            sizes.append(m)
     value = tot_inter / tot_t
+    name = f"batched_{len(boxes)}boxes" if args.workload == "batched" else boxes[0].name
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": box.name, "n": box.n, "cpd": box.cpd, "R": box.R, "eps": box.eps},
+        "higher_is_better": True, "scaling": "strong" if args.workload == "batched" else "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "n": int(sum(b.n for b in boxes)), "R": boxes[0].R,
+                   "cpd": boxes[0].cpd if len(boxes) == 1 else [b.cpd for b in boxes]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"{m} random sinks per step of the {box.n}-particle {box.name} box"},
+                         "sample": f"{int(np.mean(sizes))} random sinks per step ({'VJP' if vjp else 'accelerations'}) "
+                                   f"of the {name} workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -227,11 +246,202 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+class PlainRunner:
+    """One box (tiny, early, late): step = bin + accelerations."""
+
+    kernel = "k_pairs"
+    flops_per_pair = FLOPS_PER_PAIR
+
+    def __init__(self, args, dev):
+        import torch
+        from paper_2110_11398_gb300 import NearField
+        self.torch = torch
+        self.box = box = make_workload(args.workload)
+        self.name = box.name
+        self.n = box.n
+        self.pos = torch.from_numpy(box.pos).to(dev)
+        self.out = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
+        self.nf = NearField(box.L, box.cpd, box.eps, radius=box.R, precision=args.precision,
+                            capacity=box.n, device=dev)
+        if args.sinks_per_lane or args.warps:
+            self.nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
+                               warps_per_block=args.warps or None)
+        self.passes = 1
+
+    def step(self):
+        self.nf.bin(self.pos, gm=self.box.gm)
+        self.nf.accel(out=self.out)
+
+    def stats(self):
+        return self.nf.stats()
+
+    def config(self):
+        b = self.box
+        return {"workload": b.name, "n": b.n, "cpd": b.cpd, "R": b.R, "eps": b.eps}
+
+    def e2e(self, reps):
+        torch = self.torch
+        hpos = torch.from_numpy(self.box.pos).pin_memory().numpy()
+        hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory().numpy()
+        self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
+        return (time.perf_counter() - t0) / reps, int(hpos.nbytes), int(hacc.nbytes)
+
+    def oracle_check(self, seconds):
+        torch = self.torch
+        rate, m, inter_s, dt, idx, ref = oracle_sample(self.box, seconds)
+        got = self.out[torch.from_numpy(idx).to(self.out.device)].double().cpu().numpy()
+        sample = (f"{m} random sinks ({inter_s:.3e} interactions, {dt:.1f} s) of the "
+                  f"{self.n}-particle {self.name} box")
+        return rate, sample, got, ref
+
+    def tuning(self):
+        return self.nf.tuning
+
+    def close(self):
+        self.nf.close()
+
+
+class AdjointRunner(PlainRunner):
+    """Clustered 128^3 box: step = bin + accelerations + VJP of sum_i w_i . a_i."""
+
+    kernel = "k_vjp"
+    flops_per_pair = VJP_FLOPS_PER_PAIR
+
+    def __init__(self, args, dev):
+        super().__init__(args, dev)
+        import synth
+        self.w_np = synth.cotangent(self.n, self.box.seed)
+        self.w = self.torch.from_numpy(self.w_np).to(dev)
+        self.grad = self.torch.empty((self.n, 3), dtype=self.torch.float32, device=dev)
+        self.passes = 2
+        self.fwd_ms = []
+
+    def step(self):
+        self.nf.bin(self.pos, gm=self.box.gm)
+        self.nf.accel(out=self.out)
+        self.fwd_ms.append(self.nf.stats()["pair_ms"])
+        self.nf.vjp(self.w, out=self.grad)
+
+    def oracle_check(self, seconds):
+        import oracle
+        torch = self.torch
+        b = oracle.bin_particles(self.box.pos, self.box.L, self.box.cpd)
+        _, nsrc = oracle.interactions(b["cid"], self.box.cpd, self.box.R, per_sink=True)
+        rng = np.random.default_rng(99)
+        order = rng.permutation(self.n)
+        pos64 = self.box.pos.astype(np.float64)
+        k = 2048
+        t0 = time.perf_counter()
+        oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, self.box.eps,
+                   m0=self.box.gm, sinks=order[:k], cid=b["cid"])
+        rate = nsrc[order[:k]].sum() / max(time.perf_counter() - t0, 1e-4)
+        m = max(k, min(self.n, int(np.searchsorted(np.cumsum(nsrc[order]), rate * seconds)) + 1))
+        idx = np.sort(order[:m])
+        t0 = time.perf_counter()
+        ref = oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, self.box.eps,
+                         m0=self.box.gm, sinks=idx, cid=b["cid"])
+        dt = time.perf_counter() - t0
+        got = self.grad[torch.from_numpy(idx).to(self.grad.device)].double().cpu().numpy()
+        sample = (f"VJP on {m} random sinks ({int(nsrc[idx].sum()):.3e} interactions, {dt:.1f} s) "
+                  f"of the {self.n}-particle {self.name} box")
+        return int(nsrc[idx].sum()) / dt, sample, got, ref
+
+
+class BatchedRunner:
+    """64 independent clustered boxes in one binning and one persistent launch
+    (compute phase replayed from a CUDA graph), against the same boxes run as
+    sequential single-box contexts. Under torchrun the boxes are sharded."""
+
+    kernel = "k_pairs"
+    flops_per_pair = FLOPS_PER_PAIR
+
+    def __init__(self, args, dev, rank=0, world=1):
+        import torch
+        import synth
+        from paper_2110_11398_gb300 import NearField
+        self.torch = torch
+        allb = synth.batched()
+        self.boxes = [allb[i] for i in shard(len(allb), rank, world)]
+        self.name = f"batched_{len(allb)}boxes"
+        self.n = sum(b.n for b in self.boxes)
+        self.offs = np.cumsum([0] + [b.n for b in self.boxes])
+        self.pos = torch.from_numpy(np.concatenate([b.pos for b in self.boxes])).to(dev)
+        self.mass = torch.from_numpy(np.concatenate(
+            [np.full(b.n, b.gm, np.float32) for b in self.boxes])).to(dev)
+        self.out = torch.empty((self.n, 3), dtype=torch.float32, device=dev)
+        self.nf = NearField([b.L for b in self.boxes], [b.cpd for b in self.boxes],
+                            [b.eps for b in self.boxes], precision=args.precision,
+                            capacity=self.n, device=dev)
+        self.singles = [NearField(b.L, b.cpd, b.eps, precision=args.precision, capacity=b.n, device=dev)
+                        for b in self.boxes]
+        if args.sinks_per_lane or args.warps:
+            for nf in [self.nf] + self.singles:
+                nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
+                              warps_per_block=args.warps or None)
+        self.passes = 1
+        self.n_boxes_total = len(allb)
+
+    def step(self):
+        self.nf.bin(self.pos, self.mass, box_offsets=self.offs)
+        self.nf.accel(out=self.out)
+
+    def sequential_step(self):
+        for nf, o0, o1 in zip(self.singles, self.offs[:-1], self.offs[1:]):
+            nf.bin(self.pos[o0:o1], self.mass[o0:o1])
+            nf.accel(out=self.out[o0:o1])
+
+    def stats(self):
+        return self.nf.stats()
+
+    def config(self):
+        return {"workload": self.name, "n": self.n, "boxes": len(self.boxes),
+                "n_per_box": [int(b.n) for b in self.boxes][:64],
+                "cpd_per_box": [int(b.cpd) for b in self.boxes][:64], "R": 2}
+
+    def e2e(self, reps):
+        torch = self.torch
+        hpos = self.pos.cpu().pin_memory().numpy()
+        hmass = self.mass.cpu().pin_memory().numpy()
+        hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory().numpy()
+        self.nf.accel_host(hpos, hmass, out=hacc, box_offsets=self.offs)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            self.nf.accel_host(hpos, hmass, out=hacc, box_offsets=self.offs)
+        return (time.perf_counter() - t0) / reps, int(hpos.nbytes + hmass.nbytes), int(hacc.nbytes)
+
+    def oracle_check(self, seconds):
+        import oracle
+        torch = self.torch
+        per_box = max(16, int(300 * seconds / 15.0))
+        gots, refs, inter, dt = [], [], 0, 0.0
+        for b, o0 in zip(self.boxes, self.offs[:-1]):
+            bb = oracle.bin_particles(b.pos, b.L, b.cpd)
+            _, nsrc = oracle.interactions(bb["cid"], b.cpd, b.R, per_sink=True)
+            idx = np.sort(np.random.default_rng(b.seed).choice(b.n, min(per_box, b.n), replace=False))
+            t0 = time.perf_counter()
+            refs.append(oracle.accel(b.pos.astype(np.float64), b.L, b.cpd, b.R, b.eps, m0=b.gm,
+                                     sinks=idx, cid=bb["cid"]))
+            dt += time.perf_counter() - t0
+            inter += int(nsrc[idx].sum())
+            gots.append(self.out[torch.from_numpy(idx + o0).to(self.out.device)].double().cpu().numpy())
+        sample = f"{per_box} random sinks in each of {len(self.boxes)} boxes ({inter:.3e} interactions, {dt:.1f} s)"
+        return inter / dt, sample, np.concatenate(gots), np.concatenate(refs)
+
+    def tuning(self):
+        return self.nf.tuning
+
+    def close(self):
+        self.nf.close()
+        for nf in self.singles:
+            nf.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
-
-    from paper_2110_11398_gb300 import NearField
 
     rank, world, local = dist_env()
     if world > 1:
@@ -240,25 +450,22 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
     peaks, peak_kind = measured_peaks()
+    dist_or_none = dist if world > 1 else None
 
-    box = make_workload(args.workload)
-    n = box.n
-    pos = torch.from_numpy(box.pos).to(dev)
-    out = torch.empty((n, 3), dtype=torch.float32, device=dev)
-    nf = NearField(box.L, box.cpd, box.eps, radius=box.R, precision=args.precision,
-                   capacity=n, device=dev)
-    if args.sinks_per_lane or args.warps:
-        nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None, warps_per_block=args.warps or None)
+    if args.workload == "batched":
+        run = BatchedRunner(args, dev, rank, world)
+        scaling = "strong"
+    elif args.workload == "adjoint":
+        run = AdjointRunner(args, dev)
+        scaling = "weak"
+    else:
+        run = PlainRunner(args, dev)
+        scaling = "weak"
 
-    def step():
-        nf.bin(pos, gm=box.gm)
-        nf.accel(out=out)
-
-    # warm-up (also captures the compute graph)
-    for _ in range(args.warmup):
-        step()
+    for _ in range(args.warmup):          # warm-up (also captures the graphs)
+        run.step()
     torch.cuda.synchronize()
-    stats0 = nf.stats()
+    stats0 = run.stats()
     interactions = stats0["interactions"]
 
     clocks = ClockSampler(local)
@@ -267,15 +474,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    launches0 = nf.stats()["kernel_launches"]
+    launches0 = run.stats()["kernel_launches"]
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     pair_ms, bin_ms = [], []
     e0.record(stream)
     for _ in range(args.steps):
-        step()
-        st = nf.stats()
+        run.step()
+        st = run.stats()
         pair_ms.append(st["pair_ms"])
         bin_ms.append(st["bin_ms"])
     e1.record(stream)
@@ -284,82 +491,102 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = e0.elapsed_time(e1)
-    launches = nf.stats()["kernel_launches"] - launches0
-    ms_max, units = aggregate(elapsed_ms, interactions * args.steps, dist if world > 1 else None)
+    launches = run.stats()["kernel_launches"] - launches0
+    units_local = interactions * run.passes * args.steps
+    ms_max, units = aggregate(elapsed_ms, units_local, dist_or_none)
     ms_per_step = ms_max / args.steps
     value = units / (ms_max / 1e3)
-    updates = world * n * args.steps / (ms_max / 1e3)
+    _, n_all = aggregate(0.0, run.n, dist_or_none)
+    updates = n_all * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (the pair kernel), from its live duration
-    pair_avg = float(np.mean(pair_ms))
+    # roofline of the dominant kernel, from its live duration on this stream
+    kern_avg = float(np.mean(pair_ms))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
-    achieved = interactions * FLOPS_PER_PAIR / (pair_avg / 1e3) / 1e12
+    flops = interactions * run.flops_per_pair
+    achieved = flops / (kern_avg / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": None,
             "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                          f"(sm_max_mhz, {peak_kind})",
-            "kernel": "k_pairs", "pair_ms": pair_avg,
-            "flops_per_launch": interactions * FLOPS_PER_PAIR}
+            "kernel": run.kernel, "kernel_ms": kern_avg, "flops_per_launch": flops,
+            "flops_per_interaction": run.flops_per_pair}
     if clk.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / fp32_peak_tflops(props.multi_processor_count, clk["sm_mhz"])
     bin_avg = float(np.mean(bin_ms))
     # algorithmic bytes of the binning: read positions (12 B), write the
     # cell-sorted record (16 B) and the permutation (4 B) per particle, plus
     # the per-cell count and start (8 B per cell)
-    bin_bytes = 32 * n + 8 * stats0["n_cells"]
+    bin_bytes = 32 * run.n + 8 * stats0["n_cells"]
     roof_bin = {"bound": "hbm", "achieved": bin_bytes / (bin_avg / 1e3) / 1e9,
-                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "bin_ms": bin_avg}
+                "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "bin_ms": bin_avg,
+                "bytes_per_launch": bin_bytes}
     roof_bin["frac"] = roof_bin["achieved"] / roof_bin["peak"]
+    extra = {}
+    if isinstance(run, AdjointRunner):
+        fwd = float(np.mean(run.fwd_ms[-args.steps:]))
+        extra["forward_pair_ms"] = fwd
+        extra["vjp_over_forward"] = kern_avg / fwd
+    if isinstance(run, BatchedRunner):
+        for _ in range(2):
+            run.sequential_step()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            run.sequential_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms, _ = aggregate(s0.elapsed_time(s1), 0.0, dist_or_none)
+        extra["sequential_ms_per_step"] = seq_ms / args.steps
+        extra["sequential_value"] = units / (seq_ms / 1e3)
+        extra["batched_speedup"] = seq_ms / ms_max
 
-    # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
-        hpos = torch.from_numpy(box.pos).pin_memory().numpy()
-        hacc = torch.empty((n, 3), dtype=torch.float32).pin_memory().numpy()
-        nf.accel_host(hpos, gm=box.gm, out=hacc)          # warm staging buffers
-        torch.cuda.synchronize()
         reps = max(1, min(args.steps, 3))
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            nf.accel_host(hpos, gm=box.gm, out=hacc)
-        dt = time.perf_counter() - t0
-        e2e = {"value": world * interactions * reps / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(hpos.nbytes), "d2h_bytes_per_step": int(hacc.nbytes),
-               "ms_per_step": 1e3 * dt / reps}
+        dt, h2d, d2h = run.e2e(reps)
+        _, e2e_units = aggregate(0.0, interactions * run.passes if not isinstance(run, AdjointRunner)
+                                 else interactions, dist_or_none)
+        dt_max, _ = aggregate(dt * 1e3, 0.0, dist_or_none)
+        e2e = {"value": e2e_units / (dt_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt_max,
+               "note": "nf_accel_host: H2D positions, bin, accelerations, D2H"}
 
-    # accuracy vs the FP64 oracle on a sample, and the timed oracle baseline
     cpu = None
     err = None
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
-        rate, m, inter_s, dt, idx, ref = oracle_sample(box, args.cpu_seconds)
-        got = out[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        rate, sample, got, ref = run.oracle_check(args.cpu_seconds)
         e = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
         err = {"median": float(np.median(e)), "p99.9": float(np.quantile(e, 0.999)),
-               "max": float(e.max()), "sinks": int(m)}
+               "max": float(e.max()), "sinks": int(len(e))}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": f"{m} random sinks ({inter_s:.3e} interactions, {dt:.1f} s) of the "
-                         f"{n}-particle {box.name} box"}
+               "sample": sample}
 
-    tuning = nf.tuning
-    nf.close()
+    tuning = run.tuning()
+    cfg = run.config()
+    run.close()
     if rank == 0:
+        cfg.update({"interactions_per_step": interactions * run.passes,
+                    "max_occupancy": stats0["max_occupancy"], "precision": args.precision,
+                    "tuning": tuning,
+                    "l2": "inputs larger than L2 (positions %.2f GB)" % (12 * run.n / 1e9),
+                    "parallelism": (f"boxes sharded x{world}" if isinstance(run, BatchedRunner)
+                                    else f"replicas x{world}")})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": box.name, "n": n, "cpd": box.cpd, "R": box.R, "eps": box.eps,
-                       "interactions_per_step": interactions, "max_occupancy": stats0["max_occupancy"],
-                       "precision": args.precision, "tuning": tuning,
-                       "l2": "inputs larger than L2 (positions %.2f GB)" % (12 * n / 1e9),
-                       "parallelism": f"replicas x{world}"},
+            "scaling": scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg,
             "particle_updates_per_s": updates,
             "fp32_peak_frac": roof["frac"],
             "roofline": roof, "roofline_binning": roof_bin,
             "clocks": clk, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -371,7 +598,7 @@ def main(argv=None):
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="late", choices=["tiny", "early", "late", "adjoint"])
+    ap.add_argument("--workload", default="late", choices=["tiny", "early", "late", "adjoint", "batched"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp64"])
     ap.add_argument("--sinks-per-lane", type=int, default=0)

@@ -336,7 +336,10 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         return fail(nullptr, oom ? NF_ENOMEM : NF_ECUDA, m);
     }
     memset(c->state_h, 0, sizeof(nf::DevState));
-    c->tune = nf_tuning{2, 4, 0, 1};
+    // default launch shape: 4 sinks per lane, 4 warps per block (FP32);
+    // the compensated variant keeps 2 sinks per lane to stay clear of spills
+    c->tune = nf_tuning{4, 4, 0, 1};
+    if (precision == NF_PREC_FP32_COMP) c->tune.sinks_per_lane = 2;
     if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1;
     *out = reinterpret_cast<nf_ctx *>(c);
     return NF_OK;

@@ -67,7 +67,7 @@ struct Ctx {
     float m0 = 0.f;
     int have_momentum = 0;
 
-    nf_tuning tune{2, 4, 0, 1};
+    nf_tuning tune{4, 4, 0, 1};
     cudaStream_t cap_stream = nullptr;             // private capture stream
     GraphSlot g_fwd, g_vjp;
     cudaStream_t last_stream = nullptr;

@@ -344,8 +344,12 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             f2_t tx[K], ty[K], tz[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
+            // lane split sp takes source pairs sp, sp + S, ...; a counted
+            // loop (trip count known on entry) unrolls cleanly
+            const int n_it = (npair - sp + S - 1) >> log2s;
 #pragma unroll 2
-            for (int pp = sp; pp < npair; pp += S) {
+            for (int it = 0; it < n_it; ++it) {
+                const int pp = sp + (it << log2s);
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
                 f2_t m2 = 0ull;
                 if (!EQ) m2 = pm[pp];
