@@ -312,26 +312,40 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             ax[k] = ay[k] = az[k] = 0ull;
             lx[k] = ly[k] = lz[k] = 0ull;
         }
-        int ci = 0;
+        int ci = 0, co = 0;   // cell stream: current neighbour cell, sources taken from it
         for (int q0 = 0; q0 < nsrc; q0 += kTile) {
             const int cntT = min(kTile, nsrc - q0);
             const int npair = (cntT + 1) >> 1;
-            for (int t = lane; t < 2 * npair; t += 32) {
-                const int q = q0 + t;
-                if (q < nsrc) {
-                    const int c = locate(pfx, a.nbr, q, ci);
-                    const float4 p = a.sorted[q + dlt[c]];
-                    const int code = ofs[c];
-                    sx[t] = p.x + (float)((code & 0xff) - a.R);
-                    sy[t] = p.y + (float)(((code >> 8) & 0xff) - a.R);
-                    sz[t] = p.z + (float)((code >> 16) - a.R);
-                    if (!EQ) sm[t] = p.w;
-                } else {
-                    sx[t] = kFarAway;
-                    sy[t] = 0.f;
-                    sz[t] = 0.f;
-                    if (!EQ) sm[t] = 0.f;
+            // fill the tile cell by cell: each cell's sources are contiguous in
+            // the sorted array and share one offset d, so the lanes copy
+            // coalesced runs and add a warp-uniform shift
+            int filled = 0;
+            while (filled < cntT && ci < a.nbr) {
+                const int p0 = pfx[ci];
+                const int left = pfx[ci + 1] - p0 - co;
+                if (left <= 0) { ++ci; co = 0; continue; }
+                const int take = min(left, cntT - filled);
+                const int base = p0 + dlt[ci] + co;
+                const int code = ofs[ci];
+                const float ox = (float)((code & 0xff) - a.R);
+                const float oy = (float)(((code >> 8) & 0xff) - a.R);
+                const float oz = (float)((code >> 16) - a.R);
+                for (int t = lane; t < take; t += 32) {
+                    const float4 p = a.sorted[base + t];
+                    sx[filled + t] = p.x + ox;
+                    sy[filled + t] = p.y + oy;
+                    sz[filled + t] = p.z + oz;
+                    if (!EQ) sm[filled + t] = p.w;
                 }
+                filled += take;
+                co += take;
+                if (take == left) { ++ci; co = 0; }
+            }
+            if ((cntT & 1) && lane == 0) {   // odd tile: pad with a source that adds 0
+                sx[cntT] = kFarAway;
+                sy[cntT] = 0.f;
+                sz[cntT] = 0.f;
+                if (!EQ) sm[cntT] = 0.f;
             }
             __syncwarp();
             const f2_t *px = reinterpret_cast<const f2_t *>(sx);
@@ -555,28 +569,38 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
             gx[k] = gy[k] = gz[k] = 0ull;
         }
         const f2_t minus3 = f2_pack(-3.0f, -3.0f);
-        int ci = 0;
+        int ci = 0, co = 0;   // cell stream, as in k_pairs
         for (int q0 = 0; q0 < nsrc; q0 += kTile) {
             const int cntT = min(kTile, nsrc - q0);
             const int npair = (cntT + 1) >> 1;
-            for (int t = lane; t < 2 * npair; t += 32) {
-                const int q = q0 + t;
-                if (q < nsrc) {
-                    const int c = locate(pfx, a.nbr, q, ci);
-                    const int j = q + dlt[c];
-                    const float4 p = a.sorted[j];
-                    const float4 wv = a.w_sorted[j];
-                    const int code = ofs[c];
-                    sx[t] = p.x + (float)((code & 0xff) - a.R);
-                    sy[t] = p.y + (float)(((code >> 8) & 0xff) - a.R);
-                    sz[t] = p.z + (float)((code >> 16) - a.R);
-                    swx[t] = wv.x; swy[t] = wv.y; swz[t] = wv.z;
-                    if (!EQ) sm[t] = p.w;
-                } else {
-                    sx[t] = kFarAway; sy[t] = 0.f; sz[t] = 0.f;
-                    swx[t] = 0.f; swy[t] = 0.f; swz[t] = 0.f;
-                    if (!EQ) sm[t] = 0.f;
+            int filled = 0;
+            while (filled < cntT && ci < a.nbr) {
+                const int p0 = pfx[ci];
+                const int left = pfx[ci + 1] - p0 - co;
+                if (left <= 0) { ++ci; co = 0; continue; }
+                const int take = min(left, cntT - filled);
+                const int base = p0 + dlt[ci] + co;
+                const int code = ofs[ci];
+                const float ox = (float)((code & 0xff) - a.R);
+                const float oy = (float)(((code >> 8) & 0xff) - a.R);
+                const float oz = (float)((code >> 16) - a.R);
+                for (int t = lane; t < take; t += 32) {
+                    const float4 p = a.sorted[base + t];
+                    const float4 wv = a.w_sorted[base + t];
+                    sx[filled + t] = p.x + ox;
+                    sy[filled + t] = p.y + oy;
+                    sz[filled + t] = p.z + oz;
+                    swx[filled + t] = wv.x; swy[filled + t] = wv.y; swz[filled + t] = wv.z;
+                    if (!EQ) sm[filled + t] = p.w;
                 }
+                filled += take;
+                co += take;
+                if (take == left) { ++ci; co = 0; }
+            }
+            if ((cntT & 1) && lane == 0) {
+                sx[cntT] = kFarAway; sy[cntT] = 0.f; sz[cntT] = 0.f;
+                swx[cntT] = 0.f; swy[cntT] = 0.f; swz[cntT] = 0.f;
+                if (!EQ) sm[cntT] = 0.f;
             }
             __syncwarp();
             const f2_t *px = reinterpret_cast<const f2_t *>(sx);
@@ -589,7 +613,9 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
             f2_t tx[K], ty[K], tz[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
-            for (int pp = sp; pp < npair; pp += S) {
+            const int n_it = (npair - sp + S - 1) >> log2s;
+            for (int it = 0; it < n_it; ++it) {
+                const int pp = sp + (it << log2s);
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
                 const f2_t wx2 = pwx[pp], wy2 = pwy[pp], wz2 = pwz[pp];
                 f2_t m2 = 0ull;
