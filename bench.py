@@ -108,6 +108,12 @@ def fp32_peak_tflops(sm_count: int, mhz: float) -> float:
     return sm_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def fp64_peak_tflops(sm_count: int, mhz: float) -> float:
+    """FP64 peak of GB300: SMs x 2 DFMA per clock x 2 flops x clock
+    (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak 2 per SM cycle)."""
+    return sm_count * 2 * 2 * mhz * 1e6 / 1e12
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -527,17 +533,22 @@ def run_ours(args):
     # roofline of the dominant kernel, from its live duration on this stream
     kern_avg = float(np.mean(pair_ms))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    fp64 = args.precision == "fp64"
+    peak_fn = fp64_peak_tflops if fp64 else fp32_peak_tflops
+    peak = peak_fn(props.multi_processor_count, sm_max)
     flops = interactions * run.flops_per_pair
     achieved = flops / (kern_avg / 1e3) / 1e12
+    kernel = run.kernel + ("_f64" if fp64 else "")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": captured_traffic(run.name, run.kernel),
-            "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                         f"(sm_max_mhz, {peak_kind})",
-            "kernel": run.kernel, "kernel_ms": kern_avg, "flops_per_launch": flops,
+            "frac": achieved / peak,
+            "traffic": None if args.precision != "fp32" else captured_traffic(run.name, run.kernel),
+            "peak_note": (f"{props.multi_processor_count} SMs x 2 DFMA x 2 x {sm_max:.0f} MHz (FP64)" if fp64 else
+                          f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz")
+                         + f" (sm_max_mhz, {peak_kind})",
+            "kernel": kernel, "kernel_ms": kern_avg, "flops_per_launch": flops,
             "flops_per_interaction": run.flops_per_pair}
     if clk.get("sm_mhz"):
-        roof["frac_at_observed_clock"] = achieved / fp32_peak_tflops(props.multi_processor_count, clk["sm_mhz"])
+        roof["frac_at_observed_clock"] = achieved / peak_fn(props.multi_processor_count, clk["sm_mhz"])
     bin_avg = float(np.mean(bin_ms))
     # algorithmic bytes of the binning: read positions (12 B), write the
     # cell-sorted record (16 B) and the permutation (4 B) per particle, plus
@@ -603,10 +614,10 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": scaling, "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": cfg,
             "particle_updates_per_s": updates,
-            "fp32_peak_frac": roof["frac"],
+            "fp32_peak_frac": None if fp64 else roof["frac"],
             "roofline": roof, "roofline_binning": roof_bin,
             "clocks": clk, "gpu_launches": int(launches),
             "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
