@@ -32,7 +32,9 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-FLOPS_PER_PAIR = 20          # Plummer pair: 3 sub, 3 fma, rsqrt (2), 2 mul, 3 fma
+FLOPS_PER_PAIR = 20          # Plummer pair: 3 sub, 3 fma, rsqrt (2), 3 mul (r^3, m), 3 fma
+SPLINE_EXTRA_FLOPS = 6       # r = s rsqrt(s), two fma for the polynomial, min
+KDE_EXTRA_FLOPS = 4          # fma for 1 - r^2/b^2, max with 0, add
 VJP_FLOPS_PER_PAIR = 45      # adjoint pair (see the design notes)
 METRIC = "near-field pair interactions/s"
 UNIT = "interactions/s"
@@ -292,23 +294,39 @@ class PlainRunner:
         self.n = box.n
         self.pos = torch.from_numpy(box.pos).to(dev)
         self.out = torch.empty((box.n, 3), dtype=torch.float32, device=dev)
-        self.nf = NearField(box.L, box.cpd, box.eps, radius=box.R, precision=args.precision,
-                            capacity=box.n, device=dev)
+        self.law = getattr(args, "softening", "plummer")
+        # spline radius: the central potential -2.5/eps_s equals the Plummer -1/eps
+        eps = 2.5 * box.eps if self.law == "spline" else box.eps
+        self.nf = NearField(box.L, box.cpd, eps, radius=box.R, precision=args.precision,
+                            capacity=box.n, device=dev, softening=self.law)
         if args.sinks_per_lane or args.warps:
             self.nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
                                warps_per_block=args.warps or None)
         self.passes = 1
+        self.kde_b = 0.4 * box.L / box.n ** (1.0 / 3.0) if getattr(args, "kde", False) else None
+        self.dens = torch.empty(box.n, dtype=torch.float32, device=dev) if self.kde_b else None
+        self.flops_per_pair = (FLOPS_PER_PAIR + (SPLINE_EXTRA_FLOPS if self.law == "spline" else 0)
+                               + (KDE_EXTRA_FLOPS if self.kde_b else 0))
 
     def step(self):
         self.nf.bin(self.pos, gm=self.box.gm)
-        self.nf.accel(out=self.out)
+        if self.kde_b:
+            self.nf.accel_density(self.kde_b, out=self.out, density=self.dens)
+        else:
+            self.nf.accel(out=self.out)
 
     def stats(self):
         return self.nf.stats()
 
     def config(self):
         b = self.box
-        return {"workload": b.name, "n": b.n, "cpd": b.cpd, "R": b.R, "eps": b.eps}
+        cfg = {"workload": b.name, "n": b.n, "cpd": b.cpd, "R": b.R, "eps": b.eps,
+               "softening": self.law}
+        if self.law == "spline":
+            cfg["eps_spline"] = 2.5 * b.eps
+        if self.kde_b:
+            cfg["kde_b"] = self.kde_b
+        return cfg
 
     def e2e(self, reps):
         torch = self.torch
@@ -322,6 +340,20 @@ class PlainRunner:
 
     def oracle_check(self, seconds):
         torch = self.torch
+        if self.law != "plummer" or self.kde_b:
+            import oracle
+            idx = np.sort(np.random.default_rng(5).choice(self.n, 4000, replace=False))
+            eps = 2.5 * self.box.eps if self.law == "spline" else self.box.eps
+            t0 = time.perf_counter()
+            res = oracle.accel_ex(self.box.pos, self.box.L, self.box.cpd, self.box.R, eps, law=self.law,
+                                  kde_b=self.kde_b or 0.0, m0=self.box.gm, sinks=idx)
+            dt = time.perf_counter() - t0
+            ref = res[0] if self.kde_b else res
+            got = self.out[torch.from_numpy(idx).to(self.out.device)].double().cpu().numpy()
+            b = oracle.bin_particles(self.box.pos, self.box.L, self.box.cpd)
+            _, nsrc = oracle.interactions(b["cid"], self.box.cpd, self.box.R, per_sink=True)
+            inter = int(nsrc[idx].sum())
+            return inter / dt, f"{len(idx)} random sinks ({self.law}{', density' if self.kde_b else ''})", got, ref
         rate, m, inter_s, dt, idx, ref = oracle_sample(self.box, seconds)
         got = self.out[torch.from_numpy(idx).to(self.out.device)].double().cpu().numpy()
         sample = (f"{m} random sinks ({inter_s:.3e} interactions, {dt:.1f} s) of the "
@@ -349,6 +381,7 @@ class AdjointRunner(PlainRunner):
         self.grad = self.torch.empty((self.n, 3), dtype=self.torch.float32, device=dev)
         self.passes = 2
         self.fwd_ms = []
+        self.flops_per_pair = VJP_FLOPS_PER_PAIR
 
     def step(self):
         self.nf.bin(self.pos, gm=self.box.gm)
@@ -538,10 +571,12 @@ def run_ours(args):
     peak = peak_fn(props.multi_processor_count, sm_max)
     flops = interactions * run.flops_per_pair
     achieved = flops / (kern_avg / 1e3) / 1e12
-    kernel = run.kernel + ("_f64" if fp64 else "")
+    kernel = run.kernel + ("_f64" if fp64 else "") + ("_spline" if getattr(run, "law", "") == "spline" else "") \
+        + ("_kde" if getattr(run, "kde_b", None) else "")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
-            "traffic": None if args.precision != "fp32" else captured_traffic(run.name, run.kernel),
+            "traffic": (captured_traffic(run.name, run.kernel)
+                        if args.precision == "fp32" and kernel == run.kernel else None),
             "peak_note": (f"{props.multi_processor_count} SMs x 2 DFMA x 2 x {sm_max:.0f} MHz (FP64)" if fp64 else
                           f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz")
                          + f" (sm_max_mhz, {peak_kind})",
@@ -637,6 +672,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="late", choices=["tiny", "early", "late", "adjoint", "batched"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp64"])
+    ap.add_argument("--softening", default="plummer", choices=["plummer", "spline"])
+    ap.add_argument("--kde", action="store_true", help="also compute the kernel density estimate")
     ap.add_argument("--sinks-per-lane", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -58,7 +58,14 @@ typedef enum nf_status {
 } nf_status;
 
 typedef enum nf_softening {
-    NF_SOFT_PLUMMER = 0     /* Plummer law above (Sec. 5.2) */
+    NF_SOFT_PLUMMER = 0,    /* Plummer law above (Sec. 5.2) */
+    NF_SOFT_SPLINE = 1      /* spline law that is exactly Newtonian for r >= eps
+                               (Sec. 2.4, Sec. 5.2): inside, the pair force is
+                               G m r (10 - 15 u + 6 u^2) / eps^3 with u = r / eps,
+                               the lowest-order r P(r/eps) meeting 1/r^2 at eps
+                               with continuous first and second derivatives; eps
+                               is the radius where the law becomes 1/r^2.
+                               FP32 precision, forward pass only. */
 } nf_softening;
 
 typedef enum nf_precision {
@@ -102,7 +109,7 @@ typedef struct nf_tuning {
  *   cpd        host [n_boxes]: cells per dimension of each box, 2R+1 <= CPD <= 1024
  *   radius     near-field radius R in cells, 1..3 (the paper uses 2; Sec. 3.1)
  *   eps        host [n_boxes]: Plummer softening length of each box (> 0)
- *   softening  NF_SOFT_PLUMMER
+ *   softening  NF_SOFT_PLUMMER, or NF_SOFT_SPLINE (with NF_PREC_FP32 only)
  *   precision  an nf_precision value
  *   capacity   largest total particle count that will be binned (< 2^31)
  * Allocates all device buffers for `capacity` particles up front.
@@ -145,6 +152,22 @@ NF_API int nf_compute_accel(nf_ctx *ctx, float *acc, void *stream);
  *   acc     device [N x 3] float64 out, input particle order
  */
 NF_API int nf_compute_accel_f64(nf_ctx *ctx, double *acc, void *stream);
+
+/*
+ * nf_compute_accel_density -- nf_compute_accel plus, in the same pair pass,
+ * the kernel density estimate with which halo finding starts (Sec. 3.3):
+ *     density_i = sum_{j near i} G m_j max(0, 1 - r_ij^2 / b^2),
+ * over the same (2R+1)^3 cells, self pair included (it adds G m_i). The
+ * paper takes b = 0.4 of the mean interparticle spacing; the sum is the
+ * unnormalised kernel sum (divide by 8 pi b^3 / 15 for a mass density).
+ *   acc      device [N x 3] float32 out, input order
+ *   density  device [N] float32 out, input order
+ *   kde_b    host [n_boxes]: b of each box, 0 < b <= R * L / CPD (so that
+ *            every particle within b lies in the near field)
+ * NF_PREC_FP32 contexts only. Returns NF_OK, NF_EINVAL, NF_ESTATE, NF_ECUDA.
+ */
+NF_API int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, const double *kde_b,
+                                    void *stream);
 
 /*
  * nf_compute_accel_vjp -- vector-Jacobian product of the accelerations with

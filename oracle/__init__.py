@@ -56,6 +56,8 @@ def _load():
             lib.orc_accel.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, i64, vp]
             lib.orc_accel.restype = i32
             lib.orc_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, vp, i64, vp]
+            lib.orc_accel_ex.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, i32, dbl, vp, i64, vp, vp]
+            lib.orc_accel_ex.restype = i32
             lib.orc_vjp.restype = i32
             lib.orc_interactions.argtypes = [i64, vp, i32, i32, vp]
             lib.orc_interactions.restype = i64
@@ -129,6 +131,28 @@ def accel(pos, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float =
                              int(cpd), int(R), float(eps), _ptr(sinks), ns, _ptr(out)),
            "orc_accel")
     return out
+
+
+LAWS = {"plummer": 0, "spline": 1}
+
+
+def accel_ex(pos, L: float, cpd: int, R: int, eps: float, *, law: str = "plummer",
+             kde_b: float = 0.0, mass=None, m0: float = 1.0, sinks=None, cid=None):
+    """Near-field accelerations with the Plummer law (Sec. 5.2) or the spline
+    law that returns to 1/r^2 at r >= eps (Sec. 2.4, 5.2), and, for kde_b > 0,
+    the kernel density estimate sum_j m_j (1 - r^2/b^2)_+ (Sec. 3.3).
+    Returns acc, or (acc, density) when kde_b > 0."""
+    if cid is None:
+        cid = bin_particles(np.asarray(pos, np.float32), L, cpd)["cid"]
+    pos, cid, mass, sinks = _prep(pos, cid, mass, sinks)
+    n = pos.shape[0]
+    ns = n if sinks is None else sinks.shape[0]
+    out = np.empty((ns, 3), np.float64)
+    dens = np.empty(ns, np.float64) if kde_b > 0 else None
+    _check(_load().orc_accel_ex(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L), int(cpd),
+                                int(R), float(eps), LAWS[law], float(kde_b), _ptr(sinks), ns,
+                                _ptr(out), _ptr(dens)), "orc_accel_ex")
+    return (out, dens) if kde_b > 0 else out
 
 
 def vjp(pos, w, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float = 1.0,

@@ -207,6 +207,84 @@ int orc_accel(int64_t n, const double *pos, const int32_t *cid, const double *ma
 }
 
 /*
+ * orc_accel_ex: the near-field sum of orc_accel with a choice of pair law,
+ * plus the kernel density estimate of Sec. 3.3.
+ *   law 0 (Plummer, Sec. 5.2): f(r) = (r^2 + eps^2)^(-3/2)
+ *   law 1 (spline): the force returns to exactly 1/r^2 at r >= eps (Sec. 2.4,
+ *       Sec. 5.2 describe such a spline without printing it); inside,
+ *       F(r) = r (10 - 15 u + 6 u^2) / eps^3 with u = r / eps, the lowest-order
+ *       form r P(u) that meets 1/r^2 at u = 1 with continuous first and second
+ *       derivatives. Here eps is the radius where the law becomes 1/r^2.
+ *   The acceleration term is m_j f(r) Delta with f = F / r.
+ *   kde_b > 0: dens[q] = sum_j m_j (1 - r^2 / b^2) over the same
+ *       neighbourhood for r < b (Sec. 3.3: weighting 1 - r^2/b^2), self pair
+ *       included (it adds m_i). dens may be NULL when kde_b <= 0.
+ */
+int orc_accel_ex(int64_t n, const double *pos, const int32_t *cid, const double *mass,
+                 double m0, double L, int cpd, int R, double eps, int law, double kde_b,
+                 const int64_t *sinks, int64_t ns, double *acc, double *dens)
+{
+    if (n < 0 || cpd < 1 || R < 0 || !(L > 0.0) || !(eps > 0.0)) return ORC_EINVAL;
+    if (2 * R + 1 > cpd || law < 0 || law > 1) return ORC_EINVAL;
+    if (kde_b > 0.0 && !dens) return ORC_EINVAL;
+    int64_t ncell = (int64_t)cpd * cpd * cpd;
+    int64_t *start, *list;
+    int rc = build_lists(n, cid, ncell, &start, &list);
+    if (rc) return rc;
+    if (!sinks) ns = n;
+    const double eps2 = eps * eps, b2 = kde_b * kde_b;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < ns; ++q) {
+        int64_t i = sinks ? sinks[q] : q;
+        int c = cid[i];
+        int cx = c / (cpd * cpd), cy = (c / cpd) % cpd, cz = c % cpd;
+        double ax = 0.0, ay = 0.0, az = 0.0, rho = 0.0;
+        for (int dx = -R; dx <= R; ++dx)
+        for (int dy = -R; dy <= R; ++dy)
+        for (int dz = -R; dz <= R; ++dz) {
+            int tx = cx + dx, ty = cy + dy, tz = cz + dz;
+            int wx = wrap(tx, cpd), wy = wrap(ty, cpd), wz = wrap(tz, cpd);
+            double sx = (double)((tx - wx) / cpd) * L;
+            double sy = (double)((ty - wy) / cpd) * L;
+            double sz = (double)((tz - wz) / cpd) * L;
+            int64_t cc = ((int64_t)wx * cpd + wy) * cpd + wz;
+            for (int64_t k = start[cc]; k < start[cc + 1]; ++k) {
+                int64_t j = list[k];
+                double ddx = (pos[3 * j + 0] - pos[3 * i + 0]) + sx;
+                double ddy = (pos[3 * j + 1] - pos[3 * i + 1]) + sy;
+                double ddz = (pos[3 * j + 2] - pos[3 * i + 2]) + sz;
+                double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                double mj = mass ? mass[j] : m0;
+                double f;
+                if (law == 0) {
+                    double s = r2 + eps2;
+                    f = 1.0 / (s * sqrt(s));
+                } else {
+                    double r = sqrt(r2);
+                    if (r >= eps) {
+                        f = r2 > 0.0 ? 1.0 / (r2 * r) : 0.0;
+                    } else {
+                        double u = r / eps;
+                        f = (10.0 - 15.0 * u + 6.0 * u * u) / (eps2 * eps);
+                    }
+                }
+                ax += mj * f * ddx;
+                ay += mj * f * ddy;
+                az += mj * f * ddz;
+                if (kde_b > 0.0 && r2 < b2) rho += mj * (1.0 - r2 / b2);
+            }
+        }
+        acc[3 * q + 0] = ax;
+        acc[3 * q + 1] = ay;
+        acc[3 * q + 2] = az;
+        if (kde_b > 0.0) dens[q] = rho;
+    }
+    free(start);
+    free(list);
+    return ORC_OK;
+}
+
+/*
  * orc_vjp: vector-Jacobian product of the near-field accelerations with
  * respect to the positions, for the scalar  Lw = sum_i w_i . a_i  with the
  * binning held fixed.

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnf.so")
 
 NF_OK, NF_EINVAL, NF_ERANGE, NF_ENOMEM, NF_ECUDA, NF_ESTATE, NF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-NF_SOFT_PLUMMER = 0
+NF_SOFT_PLUMMER, NF_SOFT_SPLINE = 0, 1
+SOFTENINGS = {"plummer": NF_SOFT_PLUMMER, "spline": NF_SOFT_SPLINE}
 NF_PREC_FP32, NF_PREC_FP32_COMP, NF_PREC_FP64_REF = 0, 1, 2
 PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_PREC_FP64_REF}
 
@@ -21,6 +22,7 @@ PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_P
 EXPORTS = ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
            "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
            "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
+           "nf_compute_accel_density",
            "nf_last_error", "nf_status_string", "nf_free")
 
 
@@ -72,6 +74,7 @@ def load(path: str | None = None):
         lib.nf_compute_accel.argtypes = [vp, vp, vp]
         lib.nf_compute_accel_f64.argtypes = [vp, vp, vp]
         lib.nf_compute_accel_vjp.argtypes = [vp, vp, vp, vp]
+        lib.nf_compute_accel_density.argtypes = [vp, vp, vp, P(dbl), vp]
         lib.nf_accel_host.argtypes = [vp, vp, vp, dbl, i64, P(i64), vp, vp]
         lib.nf_get_stats.argtypes = [vp, P(nf_stats)]
         lib.nf_set_tuning.argtypes = [vp, P(nf_tuning)]
@@ -87,7 +90,8 @@ def load(path: str | None = None):
         lib.nf_free.restype = None
         for name in ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
                      "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
-                     "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc"):
+                     "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
+                     "nf_compute_accel_density"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

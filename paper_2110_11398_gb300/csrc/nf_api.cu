@@ -120,11 +120,11 @@ cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
 
 // The compute phase: work list, pair kernel, momentum diagnostic and the
 // copy of the counters to pinned host memory.
-cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
+cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nullptr) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
     if ((e = record_timing(c->ev_pair0, s))) return e;
-    if ((e = nf::launch_pairs(c, acc, f64, c->tune, s))) return e;
+    if ((e = nf::launch_pairs(c, acc, f64, c->tune, s, dens))) return e;
     if ((e = record_timing(c->ev_pair1, s))) return e;
     if ((e = nf::launch_momentum(c, acc, f64, s))) return e;
     if ((e = cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s)))
@@ -180,7 +180,7 @@ cudaError_t run_graph(Ctx *c, nf::GraphSlot &slot, const std::vector<uint64_t> &
     return cudaGraphLaunch(slot.exec, s);
 }
 
-int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
+int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nullptr) {
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel: no binned particles (call nf_bin_particles first)");
     if (!acc && c->n > 0) return fail(c, NF_EINVAL, "nf_compute_accel: acc is NULL");
     int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
@@ -190,10 +190,11 @@ int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s) {
         std::vector<uint64_t> key = {(uint64_t)(uintptr_t)acc, (uint64_t)f64, (uint64_t)c->n,
                                      (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
                                      (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
-                                     (uint64_t)c->equal_mass};
-        e = run_graph(c, c->g_fwd, key, [&](cudaStream_t cs) { return enqueue_forward(c, acc, f64, cs); }, s);
+                                     (uint64_t)c->equal_mass, (uint64_t)(uintptr_t)dens};
+        e = run_graph(c, c->g_fwd, key,
+                      [&](cudaStream_t cs) { return enqueue_forward(c, acc, f64, cs, dens); }, s);
     } else {
-        e = enqueue_forward(c, acc, f64, s);
+        e = enqueue_forward(c, acc, f64, s, dens);
     }
     if (e) return cuda_fail(c, e, "nf_compute_accel");
     c->have_momentum = 1;
@@ -238,9 +239,12 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     if (!box_size || !cpd || !eps) return fail(nullptr, NF_EINVAL, "nf_init: box_size, cpd and eps are required");
     if (radius < 1 || radius > nf::kMaxRadius)
         return fail(nullptr, NF_EINVAL, "nf_init: radius must be 1, 2 or 3");
-    if (softening != NF_SOFT_PLUMMER) return fail(nullptr, NF_EINVAL, "nf_init: unsupported softening");
+    if (softening != NF_SOFT_PLUMMER && softening != NF_SOFT_SPLINE)
+        return fail(nullptr, NF_EINVAL, "nf_init: unsupported softening");
     if (precision < NF_PREC_FP32 || precision > NF_PREC_FP64_REF)
         return fail(nullptr, NF_EINVAL, "nf_init: unknown precision");
+    if (softening == NF_SOFT_SPLINE && precision != NF_PREC_FP32)
+        return fail(nullptr, NF_EINVAL, "nf_init: the spline softening is implemented for NF_PREC_FP32");
     if (capacity < 0 || capacity >= ((int64_t)1 << 31) - 1)
         return fail(nullptr, NF_EINVAL, "nf_init: capacity must be in [0, 2^31 - 1)");
     int64_t n_cells = 0;
@@ -271,6 +275,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     c->n_boxes = n_boxes;
     c->R = radius;
     c->precision = precision;
+    c->softening = softening;
     c->capacity = capacity;
     c->n_cells = n_cells;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -289,6 +294,16 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         B.eps2 = (float)B.eps2_d;
         B.inv_h2 = (float)B.inv_h2_d;
         B.inv_h3 = (float)B.inv_h3_d;
+        if (softening == NF_SOFT_SPLINE) {
+            // pair factor inside eps_s: (10 - 15 u + 6 u^2) / eps_s^3, u = r / eps_s,
+            // as c0 + c1 r + c2 r^2 in cell units; s gets a 1e-30 floor instead of eps^2
+            const double e = eps[b] / h;
+            B.sp_c0 = (float)(10.0 / (e * e * e));
+            B.sp_c1 = (float)(-15.0 / (e * e * e * e));
+            B.sp_c2 = (float)(6.0 / (e * e * e * e * e));
+            B.eps2_d = 0.0;
+            B.eps2 = 1e-30f;
+        }
         c->boxes_h.push_back(B);
         if (!is_pow2(L)) c->pow2_all = 0;
         off += (int64_t)cpd[b] * cpd[b] * cpd[b];
@@ -412,12 +427,45 @@ int nf_compute_accel_f64(nf_ctx *ctx, double *acc, void *stream) {
     return compute_forward(c, acc, 1, reinterpret_cast<cudaStream_t>(stream));
 }
 
+int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, const double *kde_b,
+                             void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_accel_density: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (c->precision != NF_PREC_FP32)
+        return fail(c, NF_EINVAL, "nf_compute_accel_density: NF_PREC_FP32 contexts only");
+    if (!kde_b) return fail(c, NF_EINVAL, "nf_compute_accel_density: kde_b is required");
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_density: no binned particles");
+    if (c->n > 0 && !density) return fail(c, NF_EINVAL, "nf_compute_accel_density: density is NULL");
+    bool changed = false;
+    for (int b = 0; b < c->n_boxes; ++b) {
+        nf::BoxDev &B = c->boxes_h[b];
+        const double h = B.L / B.cpd;
+        if (!(kde_b[b] > 0.0) || !(kde_b[b] <= c->R * h))
+            return fail(c, NF_EINVAL, "nf_compute_accel_density: kde_b must satisfy 0 < b <= R L / CPD");
+        // 1 - r^2/b^2 = kb0 + kb1 s with s = r^2 + eps2 (cell units)
+        const double bc2 = (kde_b[b] / h) * (kde_b[b] / h);
+        const float kb1 = (float)(-1.0 / bc2);
+        const float kb0 = (float)(1.0 + (double)B.eps2 / bc2);
+        if (B.kb0 != kb0 || B.kb1 != kb1) { B.kb0 = kb0; B.kb1 = kb1; changed = true; }
+    }
+    if (changed) {
+        NF_CK(c, cudaStreamSynchronize(s));
+        NF_CK(c, cudaMemcpy(c->boxes_d, c->boxes_h.data(), sizeof(nf::BoxDev) * c->n_boxes,
+                            cudaMemcpyHostToDevice));
+    }
+    return compute_forward(c, acc, 0, s, density);
+}
+
 int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_accel_vjp: ctx is NULL");
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_vjp: no binned particles");
+    if (c->softening != NF_SOFT_PLUMMER)
+        return fail(c, NF_EINVAL, "nf_compute_accel_vjp: the adjoint is implemented for the Plummer law");
     if (c->n > 0 && (!w || !grad_pos)) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: w and grad_pos are required");
     int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
     if (rc) return rc;

@@ -24,6 +24,7 @@ struct Ctx {
     int n_boxes = 0;
     int R = 2;
     int precision = NF_PREC_FP32;
+    int softening = NF_SOFT_PLUMMER;
     int64_t capacity = 0;
     int64_t n_cells = 0;          // total over boxes
     int sm_count = 0;

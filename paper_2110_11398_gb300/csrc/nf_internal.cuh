@@ -39,9 +39,11 @@ struct BoxDev {
     double inv_h3_d;   // 1 / h^3
     int cpd;           // cells per dimension
     int cell_off;      // global id of this box's first cell
-    float eps2;        // (eps / h)^2, FP32
+    float eps2;        // (eps / h)^2, FP32 (spline law: a 1e-30 floor, see k_pairs)
     float inv_h2;      // 1 / h^2, FP32
     float inv_h3;      // 1 / h^3, FP32
+    float sp_c0, sp_c1, sp_c2;   // spline law inside eps_s: f = c0 + c1 r + c2 r^2 (cell units)
+    float kb0, kb1;    // density weight 1 - r^2/b^2 written as kb0 + kb1 s
     int pad;
 };
 
@@ -113,6 +115,17 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+__device__ __forceinline__ f2_t f2_min(f2_t a, f2_t b) {
+    float a0, a1, b0, b1;
+    f2_unpack(a, a0, a1);
+    f2_unpack(b, b0, b1);
+    return f2_pack(fminf(a0, b0), fminf(a1, b1));
+}
+__device__ __forceinline__ f2_t f2_max0(f2_t a) {
+    float a0, a1;
+    f2_unpack(a, a0, a1);
+    return f2_pack(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
+}
 __device__ __forceinline__ f2_t f2_rsqrt(f2_t v) {
     float a, b;
     f2_unpack(v, a, b);
@@ -136,7 +149,8 @@ struct Ctx;
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
                        cudaStream_t s);
 cudaError_t launch_worklist(Ctx *c, cudaStream_t s);
-cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s);
+cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s,
+                         float *dens = nullptr);
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);
 cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s);
 void make_decomp(int k, Decomp *d);

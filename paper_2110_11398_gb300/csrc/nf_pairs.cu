@@ -210,6 +210,7 @@ struct PairArgs {
     int nbr;                   // (2R+1)^3
     int tbl;                   // per-warp table stride (ints), >= nbr + 1
     float m0;                  // equal mass (when EQ)
+    float *dens;               // N, input order: kernel density estimate (KDE kernels)
 };
 
 // Per-warp neighbourhood table: pfx[ci] = exclusive prefix of the source
@@ -275,7 +276,15 @@ __device__ __forceinline__ void two_sum1(float a, float b, float &s, float &e) {
 
 // Forward pair kernel. K sinks per lane; EQ: all masses equal (applied in
 // the epilogue); COMP: per-sink sums kept as compensated (hi, lo) pairs.
-template <int K, bool EQ, bool COMP>
+// LAW 0: Plummer, f = s^-3/2 with s = r^2 + eps^2.
+// LAW 1: spline, f = min(c0 + c1 r + c2 r^2, r^-3): the polynomial is the
+//   law inside eps_s and r^-3 outside, and the two cross only at r = eps_s
+//   (u^3 (10 - 15u + 6u^2) - 1 has derivative 30 u^2 (u-1)^2 >= 0), so the
+//   minimum selects the right branch without a divergent test. s carries a
+//   1e-30 floor so that the self pair gives a finite f times a zero offset.
+// KDE: also accumulate the density sum_j m_j max(0, 1 - r^2/b^2)
+//   (Sec. 3.3), with 1 - r^2/b^2 = kb0 + kb1 s.
+template <int K, bool EQ, bool COMP, int LAW = 0, bool KDE = false>
 __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -298,9 +307,12 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
         const BoxDev B = a.boxes[box];
         const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
         const f2_t eps2 = f2_pack(B.eps2, B.eps2);
+        const f2_t c0 = f2_pack(B.sp_c0, B.sp_c0), c1 = f2_pack(B.sp_c1, B.sp_c1);
+        const f2_t c2 = f2_pack(B.sp_c2, B.sp_c2);
+        const f2_t kb0 = f2_pack(B.kb0, B.kb0), kb1 = f2_pack(B.kb1, B.kb1);
 
         f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K];
-        f2_t lx[K], ly[K], lz[K];
+        f2_t lx[K], ly[K], lz[K], rho[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int si = g + G * k;
@@ -311,6 +323,7 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             zi[k] = f2_pack(p.z, p.z);
             ax[k] = ay[k] = az[k] = 0ull;
             lx[k] = ly[k] = lz[k] = 0ull;
+            rho[k] = 0ull;
         }
         int ci = 0, co = 0;   // cell stream: current neighbour cell, sources taken from it
         for (int q0 = 0; q0 < nsrc; q0 += kTile) {
@@ -355,9 +368,9 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             // per-tile partial sums (plain FP32): each tile's <= 64/S terms per
             // accumulator are summed afresh and then folded into the running
             // total, which keeps the rounding random walk short
-            f2_t tx[K], ty[K], tz[K];
+            f2_t tx[K], ty[K], tz[K], tr[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
+            for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = tr[k] = 0ull;
             // lane split sp takes source pairs sp, sp + S, ...; a counted
             // loop (trip count known on entry) unrolls cleanly
             const int n_it = (npair - sp + S - 1) >> log2s;
@@ -377,6 +390,14 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     s = f2_fma(dz, dz, s);
                     const f2_t r = f2_rsqrt(s);
                     f2_t f = f2_mul(f2_mul(r, r), r);
+                    if (LAW == 1) {
+                        const f2_t rr = f2_mul(s, r);
+                        f = f2_min(f2_fma(f2_fma(c2, rr, c1), rr, c0), f);
+                    }
+                    if (KDE) {
+                        const f2_t t = f2_max0(f2_fma(s, kb1, kb0));
+                        tr[k] = EQ ? f2_add(tr[k], t) : f2_fma(t, m2, tr[k]);
+                    }
                     if (!EQ) f = f2_mul(f, m2);
                     if (!COMP) {
                         tx[k] = f2_fma(f, dx, tx[k]);
@@ -397,6 +418,10 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     ay[k] = f2_add(ay[k], ty[k]);
                     az[k] = f2_add(az[k], tz[k]);
                 }
+            }
+            if (KDE) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) rho[k] = f2_add(rho[k], tr[k]);
             }
             __syncwarp();
         }
@@ -429,9 +454,17 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     v[c] = __fadd_rn(h, l);
                 }
             }
+            float dv = 0.f;
+            if (KDE) {
+                float r0, r1;
+                f2_unpack(rho[k], r0, r1);
+                dv = r0 + r1;
+                for (int o = 1; o < S; o <<= 1) dv += __shfl_xor_sync(0xffffffffu, dv, o);
+            }
             const int si = g + G * k;
             if (sp == 0 && si < w.n) {
                 const int i = a.perm[w.first + si];
+                if (KDE) a.dens[i] = EQ ? dv * a.m0 : dv;
                 if (a.out_f64) {
                     const double sc = EQ ? (double)a.m0 * B.inv_h2_d : B.inv_h2_d;
                     double *o = reinterpret_cast<double *>(a.out) + 3 * (int64_t)i;
@@ -826,8 +859,21 @@ __global__ void k_momentum_final(const double *partial, int nb, double *out) {
 template <typename F>
 void *fptr(F f) { return reinterpret_cast<void *>(f); }
 
-void *pair_kernel(int prec, int K, int eq) {
+void *pair_kernel_ext(int K, int eq, int law, int kde) {
+#define NF_SEL2(KK, EE)                                                          \
+    if (K == KK && eq == EE) {                                                   \
+        if (law == 0) return fptr(k_pairs<KK, EE, false, 0, true>);              \
+        return kde ? fptr(k_pairs<KK, EE, false, 1, true>)                       \
+                   : fptr(k_pairs<KK, EE, false, 1, false>);                     \
+    }
+    NF_SEL2(1, 0) NF_SEL2(1, 1) NF_SEL2(2, 0) NF_SEL2(2, 1) NF_SEL2(4, 0) NF_SEL2(4, 1)
+#undef NF_SEL2
+    return nullptr;
+}
+
+void *pair_kernel(int prec, int K, int eq, int law = 0, int kde = 0) {
     if (prec == NF_PREC_FP64_REF) return fptr(k_pairs_f64);
+    if (law != 0 || kde) return prec == NF_PREC_FP32 ? pair_kernel_ext(K, eq, law, kde) : nullptr;
     const bool comp = prec == NF_PREC_FP32_COMP;
 #define NF_SEL(KK)                                                                       \
     if (K == KK) {                                                                       \
@@ -902,6 +948,7 @@ PairArgs make_args(Ctx *c, void *out, int out_f64) {
     a.nbr = (2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
     a.tbl = table_stride(c->R);
     a.m0 = c->m0;
+    a.dens = nullptr;
     return a;
 }
 
@@ -971,11 +1018,15 @@ cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s) {
+cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s,
+                         float *dens) {
     const int K = c->precision == NF_PREC_FP64_REF ? 1 : t.sinks_per_lane;
-    void *fn = pair_kernel(c->precision, K, c->equal_mass);
+    const int law = c->softening == NF_SOFT_SPLINE ? 1 : 0;
+    void *fn = pair_kernel(c->precision, K, c->equal_mass, law, dens != nullptr);
     if (!fn) return cudaErrorInvalidValue;
-    return launch_generic(c, fn, 0, make_args(c, acc, out_f64), t, s);
+    PairArgs args = make_args(c, acc, out_f64);
+    args.dens = dens;
+    return launch_generic(c, fn, 0, args, t, s);
 }
 
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s) {

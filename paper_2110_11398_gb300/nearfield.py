@@ -40,7 +40,7 @@ class NearField:
     """
 
     def __init__(self, box_size, cpd, eps, *, radius: int = 2, precision: str = "fp32",
-                 capacity: int, n_boxes: int | None = None, device=None):
+                 capacity: int, n_boxes: int | None = None, device=None, softening: str = "plummer"):
         if n_boxes is None:
             n_boxes = len(cpd) if isinstance(cpd, (list, tuple, np.ndarray)) else 1
         self.n_boxes = int(n_boxes)
@@ -57,8 +57,9 @@ class NearField:
         L = (ctypes.c_double * self.n_boxes)(*self.box_size)
         C = (ctypes.c_int * self.n_boxes)(*self.cpd)
         E = (ctypes.c_double * self.n_boxes)(*self.eps)
+        self.softening = softening
         rc = self._lib.nf_init(ctypes.byref(self._ctx), self.device.index, self.n_boxes, L, C,
-                               self.radius, E, N.NF_SOFT_PLUMMER, N.PRECISIONS[precision],
+                               self.radius, E, N.SOFTENINGS[softening], N.PRECISIONS[precision],
                                self.capacity)
         N.check(rc, None, "nf_init")
         self.n = 0
@@ -140,6 +141,23 @@ class NearField:
             raise ValueError("out must be float32 or float64")
         N.check(rc, self._ctx, "nf_compute_accel")
         return out
+
+    def accel_density(self, kde_b, out: torch.Tensor | None = None,
+                      density: torch.Tensor | None = None):
+        """Accelerations and the kernel density estimate sum_j G m_j (1 - r^2/b^2)_+
+        in one pass; ``kde_b`` is b per box (or one value for all boxes)."""
+        if out is None:
+            out = torch.empty((self.n, 3), dtype=torch.float32, device=self.device)
+        out = self._check_vec3(out, "out")
+        if density is None:
+            density = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        if density.device != self.device or density.dtype != torch.float32 or density.shape != (self.n,):
+            raise ValueError("density must be an (N,) float32 tensor on the context's device")
+        B = (ctypes.c_double * self.n_boxes)(*_as_list(kde_b, self.n_boxes, float))
+        rc = self._lib.nf_compute_accel_density(self._ctx, out.data_ptr(), density.data_ptr(), B,
+                                                _stream_ptr(self.device))
+        N.check(rc, self._ctx, "nf_compute_accel_density")
+        return out, density
 
     def vjp(self, w: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """d(sum_i w_i . a_i)/dx with the current binning held fixed."""
