@@ -137,6 +137,16 @@ NF_API int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, do
                      int64_t n, const int64_t *box_offsets, void *stream);
 
 /*
+ * nf_set_box_masses -- equal masses per box: later nf_bin_particles calls
+ * with mass == NULL give every particle of box b the mass gm[b] (instead of
+ * mass_if_null), so boxes of different particle mass keep the equal-mass
+ * pair kernel (G m applied once per sink).
+ *   gm   host [n_boxes] G*m per box, or NULL to return to mass_if_null
+ * Returns NF_OK or NF_EINVAL (non-finite value).
+ */
+NF_API int nf_set_box_masses(nf_ctx *ctx, const double *gm);
+
+/*
  * nf_compute_accel -- near-field accelerations of every binned particle
  * (the direct O(N^2) near-field sum of Sec. 3.1 over (2R+1)^3 cells).
  *   acc     device [N x 3] float32 out, input particle order, caller-owned

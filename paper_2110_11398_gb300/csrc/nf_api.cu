@@ -371,7 +371,8 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
     c->binned = 0;
     if (n < 0 || n > c->capacity) return fail(c, NF_EINVAL, "nf_bin_particles: n must be in [0, capacity]");
     if (n > 0 && !pos) return fail(c, NF_EINVAL, "nf_bin_particles: pos is NULL");
-    if (!mass && !(std::isfinite(mass_if_null))) return fail(c, NF_EINVAL, "nf_bin_particles: mass_if_null must be finite");
+    if (!mass && c->box_gm.empty() && !(std::isfinite(mass_if_null)))
+        return fail(c, NF_EINVAL, "nf_bin_particles: mass_if_null must be finite");
     std::vector<int64_t> poff(c->n_boxes + 1);
     if (c->n_boxes == 1) {
         if (box_offsets && (box_offsets[0] != 0 || box_offsets[1] != n))
@@ -396,6 +397,24 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
     }
     c->equal_mass = mass ? 0 : 1;
     c->m0 = (float)mass_if_null;
+    if (!mass) {
+        // equal masses: one G m per box (nf_set_box_masses), else mass_if_null
+        bool changed = false;
+        for (int b = 0; b < c->n_boxes; ++b) {
+            const double g = c->box_gm.empty() ? mass_if_null : c->box_gm[b];
+            nf::BoxDev &B = c->boxes_h[b];
+            if (B.gm_d != (double)(float)g || B.gm != (float)g) {
+                B.gm = (float)g;
+                B.gm_d = (double)B.gm;
+                changed = true;
+            }
+        }
+        if (changed) {
+            NF_CK(c, cudaStreamSynchronize(s));
+            NF_CK(c, cudaMemcpy(c->boxes_d, c->boxes_h.data(), sizeof(nf::BoxDev) * c->n_boxes,
+                                cudaMemcpyHostToDevice));
+        }
+    }
     NF_CK(c, cudaEventRecord(c->ev_bin0, s));
     cudaError_t e = nf::launch_bin(c, pos, mass, c->m0, n, s);
     if (e) return cuda_fail(c, e, "nf_bin_particles");
@@ -410,6 +429,19 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
     }
     c->binned = 1;
     c->have_momentum = 0;
+    return NF_OK;
+}
+
+int nf_set_box_masses(nf_ctx *ctx, const double *gm) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_set_box_masses: ctx is NULL");
+    if (!gm) {
+        c->box_gm.clear();
+        return NF_OK;
+    }
+    for (int b = 0; b < c->n_boxes; ++b)
+        if (!std::isfinite(gm[b])) return fail(c, NF_EINVAL, "nf_set_box_masses: masses must be finite");
+    c->box_gm.assign(gm, gm + c->n_boxes);
     return NF_OK;
 }
 

@@ -281,7 +281,7 @@ __global__ void k_gather(const float *__restrict__ pos, const float *__restrict_
             const int c = in ? cell_index(u, B.cpd) : 0;
             r[a] = __dsub_rn(u, (double)c + 0.5);
         }
-        const float m = mass ? mass[i] : m0;
+        const float m = mass ? mass[i] : B.gm;
         sorted[k] = make_float4(__double2float_rn(r[0]), __double2float_rn(r[1]),
                                 __double2float_rn(r[2]), m);
         if (sorted_d) sorted_d[k] = dbl4_make(r[0], r[1], r[2], (double)m);
@@ -502,6 +502,8 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
     B.cell_off = 0;
     B.inv_h2_d = 1.0 / (h * h);
     B.inv_h3_d = 1.0 / (h * h * h);
+    B.gm = (float)mass_if_null;
+    B.gm_d = (double)B.gm;
     int ex = 0;
     c.pow2_all = std::frexp(box_size, &ex) == 0.5 ? 1 : 0;
     const int64_t poff[2] = {0, n};

@@ -66,6 +66,7 @@ struct Ctx {
     int binned = 0;
     int equal_mass = 1;
     float m0 = 0.f;
+    std::vector<double> box_gm;                    // per-box G m (nf_set_box_masses), empty = unset
     int have_momentum = 0;
 
     nf_tuning tune{4, 4, 0, 1};

@@ -44,7 +44,8 @@ struct BoxDev {
     float inv_h3;      // 1 / h^3, FP32
     float sp_c0, sp_c1, sp_c2;   // spline law inside eps_s: f = c0 + c1 r + c2 r^2 (cell units)
     float kb0, kb1;    // density weight 1 - r^2/b^2 written as kb0 + kb1 s
-    int pad;
+    float gm;          // G m of every particle of this box when no mass array is given
+    double gm_d;       // same, double
 };
 
 // One unit of pair work: `n` consecutive cell-sorted sinks of one cell,

@@ -209,7 +209,6 @@ struct PairArgs {
     int R;
     int nbr;                   // (2R+1)^3
     int tbl;                   // per-warp table stride (ints), >= nbr + 1
-    float m0;                  // equal mass (when EQ)
     float *dens;               // N, input order: kernel density estimate (KDE kernels)
 };
 
@@ -464,15 +463,15 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             const int si = g + G * k;
             if (sp == 0 && si < w.n) {
                 const int i = a.perm[w.first + si];
-                if (KDE) a.dens[i] = EQ ? dv * a.m0 : dv;
+                if (KDE) a.dens[i] = EQ ? dv * B.gm : dv;
                 if (a.out_f64) {
-                    const double sc = EQ ? (double)a.m0 * B.inv_h2_d : B.inv_h2_d;
+                    const double sc = EQ ? B.gm_d * B.inv_h2_d : B.inv_h2_d;
                     double *o = reinterpret_cast<double *>(a.out) + 3 * (int64_t)i;
                     o[0] = (double)v[0] * sc;
                     o[1] = (double)v[1] * sc;
                     o[2] = (double)v[2] * sc;
                 } else {
-                    const float sc = EQ ? a.m0 * B.inv_h2 : B.inv_h2;
+                    const float sc = EQ ? B.gm * B.inv_h2 : B.inv_h2;
                     float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
                     o[0] = v[0] * sc;
                     o[1] = v[1] * sc;
@@ -712,7 +711,7 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
             const int si = g + G * k;
             if (sp == 0 && si < w.n) {
                 const int i = a.perm[w.first + si];
-                const float sc = EQ ? a.m0 * B.inv_h3 : B.inv_h3;
+                const float sc = EQ ? B.gm * B.inv_h3 : B.inv_h3;
                 float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
                 o[0] = v[0] * sc;
                 o[1] = v[1] * sc;
@@ -947,7 +946,6 @@ PairArgs make_args(Ctx *c, void *out, int out_f64) {
     a.R = c->R;
     a.nbr = (2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
     a.tbl = table_stride(c->R);
-    a.m0 = c->m0;
     a.dens = nullptr;
     return a;
 }

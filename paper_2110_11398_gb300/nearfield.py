@@ -104,7 +104,11 @@ class NearField:
     # ------------------------------------------------------------ the path
     def bin(self, pos: torch.Tensor, mass: torch.Tensor | None = None, *,
             gm: float | None = None, box_offsets: Sequence[int] | None = None) -> None:
-        """Bin ``pos`` (N,3) float32 into cells and keep a cell-sorted snapshot."""
+        """Bin ``pos`` (N,3) float32 into cells and keep a cell-sorted snapshot.
+
+        Masses: a per-particle ``mass`` tensor, or ``gm`` = G*m of every
+        particle (a number) or of every particle of each box (a list).
+        """
         pos = self._check_vec3(pos, "pos")
         n = pos.shape[0]
         mptr = None
@@ -115,11 +119,18 @@ class NearField:
             mptr = mass.data_ptr()
         elif gm is None:
             raise ValueError("give either mass or gm (G*m of every particle)")
+        gm_scalar = 0.0
+        if mass is None:
+            if isinstance(gm, (list, tuple, np.ndarray)):
+                G = (ctypes.c_double * self.n_boxes)(*_as_list(gm, self.n_boxes, float))
+                N.check(self._lib.nf_set_box_masses(self._ctx, G), self._ctx, "nf_set_box_masses")
+            else:
+                N.check(self._lib.nf_set_box_masses(self._ctx, None), self._ctx, "nf_set_box_masses")
+                gm_scalar = float(gm)
         off = self._offsets(box_offsets)
         offp = None if off is None else off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         rc = self._lib.nf_bin_particles(self._ctx, pos.data_ptr() if n else None, mptr,
-                                        float(gm if gm is not None else 0.0), n, offp,
-                                        _stream_ptr(self.device))
+                                        gm_scalar, n, offp, _stream_ptr(self.device))
         N.check(rc, self._ctx, "nf_bin_particles")
         self.n = n
         self.generation += 1
@@ -184,12 +195,19 @@ class NearField:
         if mass is None and gm is None:
             raise ValueError("give either mass or gm")
         mptr = None
+        gm_scalar = 0.0
         if mass is not None:
             mass = np.ascontiguousarray(mass, dtype=np.float32)
             mptr = mass.ctypes.data
+        elif isinstance(gm, (list, tuple, np.ndarray)):
+            G = (ctypes.c_double * self.n_boxes)(*_as_list(gm, self.n_boxes, float))
+            N.check(self._lib.nf_set_box_masses(self._ctx, G), self._ctx, "nf_set_box_masses")
+        else:
+            N.check(self._lib.nf_set_box_masses(self._ctx, None), self._ctx, "nf_set_box_masses")
+            gm_scalar = float(gm)
         off = self._offsets(box_offsets)
         offp = None if off is None else off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
-        rc = self._lib.nf_accel_host(self._ctx, pos.ctypes.data, mptr, float(gm or 0.0), n, offp,
+        rc = self._lib.nf_accel_host(self._ctx, pos.ctypes.data, mptr, gm_scalar, n, offp,
                                      out.ctypes.data, _stream_ptr(self.device))
         N.check(rc, self._ctx, "nf_accel_host")
         self.n = n

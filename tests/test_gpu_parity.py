@@ -298,6 +298,28 @@ def test_batched_boxes_bit_identical_to_plain(dev):
     assert inter == tot
 
 
+def test_batched_per_box_masses_bit_identical_to_plain(dev):
+    """Per-box equal masses (nf_set_box_masses) keep the equal-mass kernel;
+    each box's result equals its own single-box context bit for bit."""
+    from paper_2110_11398_gb300 import NearField
+    boxes = synth.batched(n_boxes=5, lo_side=18, hi_side=36, seed0=11)
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    nfb = NearField([b.L for b in boxes], [b.cpd for b in boxes], [b.eps for b in boxes],
+                    capacity=int(offs[-1]), device=dev)
+    pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+    nfb.bin(pos, gm=[b.gm for b in boxes], box_offsets=offs)
+    ab = nfb.accel().cpu().numpy()
+    mom = nfb.stats()
+    nfb.close()
+    for b, o0, o1 in zip(boxes, offs[:-1], offs[1:]):
+        nf = make_nf(b, dev)
+        nf.bin(torch.from_numpy(b.pos).to(dev), gm=b.gm)
+        ap = nf.accel().cpu().numpy()
+        nf.close()
+        assert np.array_equal(ab[o0:o1].view(np.uint32), ap.view(np.uint32))
+    assert np.all(np.abs(np.array(mom["momentum"])) <= 1e-5 * mom["abs_momentum"])
+
+
 def test_autotune_picks_a_valid_shape(dev):
     box = synth.tiny()
     nf = make_nf(box, dev)
