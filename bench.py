@@ -279,6 +279,11 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def synth_box_like(box, pos):
+    import synth
+    return synth.Box(box.name, pos, box.L, box.cpd, box.eps, box.gm, box.R, box.seed, box.info)
+
+
 class PlainRunner:
     """One box (tiny, early, late): step = bin + accelerations."""
 
@@ -307,8 +312,21 @@ class PlainRunner:
         self.dens = torch.empty(box.n, dtype=torch.float32, device=dev) if self.kde_b else None
         self.flops_per_pair = (FLOPS_PER_PAIR + (SPLINE_EXTRA_FLOPS if self.law == "spline" else 0)
                                + (KDE_EXTRA_FLOPS if self.kde_b else 0))
+        self.kdk = getattr(args, "kdk", False)
+        if self.kdk:
+            # synthetic velocities, N(0, 1) in units of the mean spacing per unit
+            # time; the global timestep comes from the criterion (eta = 0.25)
+            spacing = box.L / box.n ** (1.0 / 3.0)
+            v = np.random.default_rng(box.seed + 17).standard_normal((box.n, 3)).astype(np.float32)
+            self.vel = torch.from_numpy(v * np.float32(spacing)).to(dev)
+            self.nf.bin(self.pos, gm=box.gm)
+            self.nf.accel(out=self.out)
+            self.dt = self.nf.timestep(self.vel, self.out, 0.25)
 
     def step(self):
+        if self.kdk:
+            self.nf.kdk_step(self.pos, self.vel, self.out, self.dt, gm=self.box.gm)
+            return
         self.nf.bin(self.pos, gm=self.box.gm)
         if self.kde_b:
             self.nf.accel_density(self.kde_b, out=self.out, density=self.dens)
@@ -326,6 +344,9 @@ class PlainRunner:
             cfg["eps_spline"] = 2.5 * b.eps
         if self.kde_b:
             cfg["kde_b"] = self.kde_b
+        if self.kdk:
+            cfg["step"] = "kick-drift-kick (half kick, drift, re-bin, accelerations, half kick)"
+            cfg["dt"] = self.dt
         return cfg
 
     def e2e(self, reps):
@@ -340,6 +361,10 @@ class PlainRunner:
 
     def oracle_check(self, seconds):
         torch = self.torch
+        if self.kdk:
+            # the particles have moved: check the accelerations of the current positions
+            cur = self.pos.cpu().numpy()
+            self.box = synth_box_like(self.box, cur)
         if self.law != "plummer" or self.kde_b:
             import oracle
             idx = np.sort(np.random.default_rng(5).choice(self.n, 4000, replace=False))
@@ -675,6 +700,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp64"])
     ap.add_argument("--softening", default="plummer", choices=["plummer", "spline"])
     ap.add_argument("--kde", action="store_true", help="also compute the kernel density estimate")
+    ap.add_argument("--kdk", action="store_true",
+                    help="time full leapfrog steps (kick, drift, re-bin, accelerations, kick)")
     ap.add_argument("--sinks-per-lane", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -194,6 +194,34 @@ NF_API int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, con
 NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream);
 
 /*
+ * Particle update with a global timestep (Sec. 2.4: second-order leapfrog,
+ * kick-drift-kick). All arrays are device [N x 3] float32 in input order, N
+ * and the box of each particle being those of the last nf_bin_particles.
+ *
+ * nf_kick  -- v += a dt, in double and rounded once to float32.
+ * nf_drift -- x += v dt in double, wrapped into [0, L) of the particle's box
+ *             and rounded once to float32 (a value that rounds up to L
+ *             becomes 0, its periodic image).
+ * nf_timestep -- the small-scale criterion: eta times the minimum over cells
+ *             of (3-D velocity dispersion about the cell mean) / (maximum
+ *             particle |a| in the cell); cells with fewer than two particles
+ *             or no acceleration give no bound (the result is +inf if none
+ *             does). Cells are those of the last binning. Synchronises.
+ * nf_kdk_step -- one step: v += a dt/2; x += v dt; re-bin x (same masses and
+ *             box offsets as nf_bin_particles); a = near-field accelerations
+ *             at the new x; v += a dt/2. On entry acc must hold the
+ *             accelerations of the binned positions; on exit it holds those
+ *             of the new positions. Synchronises (through the re-binning).
+ * Return NF_OK, NF_EINVAL, NF_ESTATE, NF_ERANGE (re-binning) or NF_ECUDA.
+ */
+NF_API int nf_kick(nf_ctx *ctx, float *vel, const float *acc, double dt, void *stream);
+NF_API int nf_drift(nf_ctx *ctx, float *pos, const float *vel, double dt, void *stream);
+NF_API int nf_timestep(nf_ctx *ctx, const float *vel, const float *acc, double eta, double *dt_out,
+                       void *stream);
+NF_API int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const float *mass,
+                       double mass_if_null, double dt, const int64_t *box_offsets, void *stream);
+
+/*
  * nf_accel_host -- end-to-end convenience call on HOST buffers: copies
  * positions (and masses) to the device, bins, computes the accelerations and
  * copies them back, then synchronises `stream`.

@@ -59,6 +59,8 @@ def _load():
             lib.orc_accel_ex.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, i32, dbl, vp, i64, vp, vp]
             lib.orc_accel_ex.restype = i32
             lib.orc_vjp.restype = i32
+            lib.orc_cell_timestep.argtypes = [i64, vp, vp, vp, i32, dbl]
+            lib.orc_cell_timestep.restype = dbl
             lib.orc_interactions.argtypes = [i64, vp, i32, i32, vp]
             lib.orc_interactions.restype = i64
             lib.orc_num_threads.argtypes = []
@@ -188,3 +190,40 @@ def interactions(cid, cpd: int, R: int, per_sink: bool = False):
     if tot < 0:
         raise OracleError("orc_interactions: out of memory")
     return (tot, nsrc) if per_sink else tot
+
+
+def cell_timestep(vel, acc, cid, cpd: int, eta: float = 0.25) -> float:
+    """Small-scale timestep criterion (Sec. 2.4): eta times the minimum over
+    cells of velocity dispersion / maximum particle acceleration."""
+    vel = np.ascontiguousarray(vel, dtype=np.float64)
+    acc = np.ascontiguousarray(acc, dtype=np.float64)
+    cid = np.ascontiguousarray(cid, dtype=np.int32)
+    r = float(_load().orc_cell_timestep(vel.shape[0], _ptr(vel), _ptr(acc), _ptr(cid), int(cpd),
+                                        float(eta)))
+    if r < 0:
+        raise OracleError("orc_cell_timestep failed")
+    return r
+
+
+def wrap_f32(x, L: float):
+    """Positions wrapped into [0, L) in double, then rounded to float32; a value
+    that rounds up to L is the periodic image of 0."""
+    x = np.mod(np.asarray(x, np.float64), L)
+    x32 = x.astype(np.float32)
+    x32[x32 >= np.float32(L)] = np.float32(0)
+    return x32
+
+
+def kdk_step(pos32, vel32, dt: float, L: float, cpd: int, R: int, eps: float, *, m0: float,
+             acc0=None):
+    """One second-order kick-drift-kick leapfrog step with a global timestep
+    (Sec. 2.4): v += a(x) dt/2; x += v dt (wrapped); v += a(x') dt/2, with the
+    near-field accelerations re-binned at x'. Positions and velocities are
+    float32 as on the device; the arithmetic is double. Returns
+    (pos, vel, acc at the new positions)."""
+    a0 = accel(pos32, L, cpd, R, eps, m0=m0) if acc0 is None else np.asarray(acc0, np.float64)
+    v_half = (np.asarray(vel32, np.float64) + 0.5 * dt * a0).astype(np.float32)
+    x1 = wrap_f32(np.asarray(pos32, np.float64) + dt * v_half.astype(np.float64), L)
+    a1 = accel(x1, L, cpd, R, eps, m0=m0)
+    v1 = (v_half.astype(np.float64) + 0.5 * dt * a1).astype(np.float32)
+    return x1, v1, a1

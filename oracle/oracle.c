@@ -385,3 +385,47 @@ int64_t orc_interactions(int64_t n, const int32_t *cid, int cpd, int R, int64_t 
     free(src);
     return total;
 }
+
+/*
+ * orc_cell_timestep: the small-scale timestep criterion of Sec. 2.4, the
+ * minimum over cells of (per-cell velocity dispersion) / (per-cell maximum
+ * particle acceleration), times eta. The dispersion is the 3-D rms of
+ * v - <v>_cell; cells with fewer than two particles or with all
+ * accelerations zero give no bound. Returns +inf if no cell bounds the step.
+ *   vel, acc [n*3] double; cid [n] cell of each particle.
+ */
+double orc_cell_timestep(int64_t n, const double *vel, const double *acc, const int32_t *cid,
+                         int cpd, double eta)
+{
+    int64_t ncell = (int64_t)cpd * cpd * cpd;
+    int64_t *start, *list;
+    if (build_lists(n, cid, ncell, &start, &list)) return -1.0;
+    double best = INFINITY;
+    for (int64_t c = 0; c < ncell; ++c) {
+        int64_t m = start[c + 1] - start[c];
+        if (m < 2) continue;
+        double mean[3] = {0.0, 0.0, 0.0}, amax = 0.0;
+        for (int64_t k = start[c]; k < start[c + 1]; ++k) {
+            int64_t i = list[k];
+            for (int a = 0; a < 3; ++a) mean[a] += vel[3 * i + a];
+            double a2 = acc[3 * i] * acc[3 * i] + acc[3 * i + 1] * acc[3 * i + 1] + acc[3 * i + 2] * acc[3 * i + 2];
+            if (a2 > amax) amax = a2;
+        }
+        for (int a = 0; a < 3; ++a) mean[a] /= (double)m;
+        double var = 0.0;
+        for (int64_t k = start[c]; k < start[c + 1]; ++k) {
+            int64_t i = list[k];
+            for (int a = 0; a < 3; ++a) {
+                double d = vel[3 * i + a] - mean[a];
+                var += d * d;
+            }
+        }
+        var /= (double)m;
+        if (amax <= 0.0) continue;
+        double r = sqrt(var) / sqrt(amax);
+        if (r < best) best = r;
+    }
+    free(start);
+    free(list);
+    return eta * best;
+}

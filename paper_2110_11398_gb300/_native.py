@@ -22,7 +22,8 @@ PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_P
 EXPORTS = ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
            "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
            "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
-           "nf_compute_accel_density", "nf_set_box_masses",
+           "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift", "nf_timestep",
+           "nf_kdk_step",
            "nf_last_error", "nf_status_string", "nf_free")
 
 
@@ -76,6 +77,10 @@ def load(path: str | None = None):
         lib.nf_compute_accel_vjp.argtypes = [vp, vp, vp, vp]
         lib.nf_compute_accel_density.argtypes = [vp, vp, vp, P(dbl), vp]
         lib.nf_set_box_masses.argtypes = [vp, P(dbl)]
+        lib.nf_kick.argtypes = [vp, vp, vp, dbl, vp]
+        lib.nf_drift.argtypes = [vp, vp, vp, dbl, vp]
+        lib.nf_timestep.argtypes = [vp, vp, vp, dbl, P(dbl), vp]
+        lib.nf_kdk_step.argtypes = [vp, vp, vp, vp, vp, dbl, dbl, P(i64), vp]
         lib.nf_accel_host.argtypes = [vp, vp, vp, dbl, i64, P(i64), vp, vp]
         lib.nf_get_stats.argtypes = [vp, P(nf_stats)]
         lib.nf_set_tuning.argtypes = [vp, P(nf_tuning)]
@@ -92,7 +97,8 @@ def load(path: str | None = None):
         for name in ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
                      "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
                      "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
-                     "nf_compute_accel_density", "nf_set_box_masses"):
+                     "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift",
+                     "nf_timestep", "nf_kdk_step"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

@@ -61,11 +61,13 @@ void release(Ctx *c) {
     void *bufs[] = {c->boxes_d, c->poff_d, c->keys_a, c->keys_b, c->vals_a, c->vals_b,
                     c->count, c->cell_start, c->scan_tmp, c->radix_hist, c->sorted,
                     c->sorted_d, c->w_sorted, c->nsrc_cell, c->items, c->decomp_d,
-                    c->state, c->mom_partial, c->mom_result, c->st_pos, c->st_mass, c->st_acc};
+                    c->state, c->mom_partial, c->mom_result, c->st_pos, c->st_mass, c->st_acc,
+                    c->step_bits};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->state_h) cudaFreeHost(c->state_h);
     if (c->mom_h) cudaFreeHost(c->mom_h);
+    if (c->step_bits_h) cudaFreeHost(c->step_bits_h);
     if (c->g_fwd.exec) cudaGraphExecDestroy(c->g_fwd.exec);
     if (c->g_vjp.exec) cudaGraphExecDestroy(c->g_vjp.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -333,9 +335,11 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     NF_AL(c->state, 1);
     NF_AL(c->mom_partial, (int64_t)nf::kMomBlocks * 4);
     NF_AL(c->mom_result, 4);
+    NF_AL(c->step_bits, 1);
 #undef NF_AL
     if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->state_h), sizeof(nf::DevState));
     if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->mom_h), 4 * sizeof(double));
+    if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->step_bits_h), sizeof(unsigned));
     if (!e) e = cudaMemcpy(c->boxes_d, c->boxes_h.data(), sizeof(nf::BoxDev) * n_boxes, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(c->state, 0, sizeof(nf::DevState));
     if (!e) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -515,6 +519,64 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
     c->have_pair_time = 1;
     c->last_stream = s;
     return NF_OK;
+}
+
+int nf_kick(nf_ctx *ctx, float *vel, const float *acc, double dt, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_kick: ctx is NULL");
+    DeviceGuard guard(c->device);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_kick: no binned particles");
+    if (c->n > 0 && (!vel || !acc)) return fail(c, NF_EINVAL, "nf_kick: vel and acc are required");
+    if (!std::isfinite(dt)) return fail(c, NF_EINVAL, "nf_kick: dt must be finite");
+    cudaError_t e = nf::launch_kick(c, vel, acc, dt, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(c, e, "nf_kick") : NF_OK;
+}
+
+int nf_drift(nf_ctx *ctx, float *pos, const float *vel, double dt, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_drift: ctx is NULL");
+    DeviceGuard guard(c->device);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_drift: no binned particles");
+    if (c->n > 0 && (!pos || !vel)) return fail(c, NF_EINVAL, "nf_drift: pos and vel are required");
+    if (!std::isfinite(dt)) return fail(c, NF_EINVAL, "nf_drift: dt must be finite");
+    cudaError_t e = nf::launch_drift(c, pos, vel, dt, reinterpret_cast<cudaStream_t>(stream));
+    return e ? cuda_fail(c, e, "nf_drift") : NF_OK;
+}
+
+int nf_timestep(nf_ctx *ctx, const float *vel, const float *acc, double eta, double *dt_out,
+                void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_timestep: ctx is NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_timestep: no binned particles");
+    if (!dt_out || (c->n > 0 && (!vel || !acc)))
+        return fail(c, NF_EINVAL, "nf_timestep: vel, acc and dt_out are required");
+    if (!(eta > 0.0)) return fail(c, NF_EINVAL, "nf_timestep: eta must be > 0");
+    cudaError_t e = nf::launch_cell_timestep(c, vel, acc, c->step_bits, s);
+    if (!e) e = cudaMemcpyAsync(c->step_bits_h, c->step_bits, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return cuda_fail(c, e, "nf_timestep");
+    float r;
+    memcpy(&r, c->step_bits_h, sizeof(float));
+    *dt_out = r >= 3.0e38f ? INFINITY : eta * (double)r;
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const float *mass,
+                double mass_if_null, double dt, const int64_t *box_offsets, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_kdk_step: ctx is NULL");
+    DeviceGuard guard(c->device);
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_kdk_step: bin the positions and compute acc first");
+    const int64_t n = c->n;
+    int rc;
+    if ((rc = nf_kick(ctx, vel, acc, 0.5 * dt, stream))) return rc;
+    if ((rc = nf_drift(ctx, pos, vel, dt, stream))) return rc;
+    if ((rc = nf_bin_particles(ctx, pos, mass, mass_if_null, n, box_offsets, stream))) return rc;
+    if ((rc = nf_compute_accel(ctx, acc, stream))) return rc;
+    return nf_kick(ctx, vel, acc, 0.5 * dt, stream);
 }
 
 int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, double mass_if_null,

@@ -60,6 +60,8 @@ struct Ctx {
     double *mom_partial = nullptr;                 // [kMomBlocks * 4]
     double *mom_result = nullptr;                  // [4]
     double *mom_h = nullptr;                       // pinned [4]
+    unsigned *step_bits = nullptr;                 // [1] timestep criterion (float bits)
+    unsigned *step_bits_h = nullptr;               // pinned mirror
 
     // last binning
     int64_t n = 0;

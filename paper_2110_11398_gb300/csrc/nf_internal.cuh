@@ -155,6 +155,10 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);
 cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s);
 void make_decomp(int k, Decomp *d);
+cudaError_t launch_kick(Ctx *c, float *vel, const float *acc, double h, cudaStream_t s);
+cudaError_t launch_drift(Ctx *c, float *pos, const float *vel, double dt, cudaStream_t s);
+cudaError_t launch_cell_timestep(Ctx *c, const float *vel, const float *acc, unsigned *best_bits,
+                                 cudaStream_t s);
 cudaError_t scan_exclusive(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s,
                            int64_t *launches);
 int64_t scan_tmp_ints(int64_t n);

@@ -183,6 +183,51 @@ class NearField:
         N.check(rc, self._ctx, "nf_compute_accel_vjp")
         return out
 
+    # ------------------------------------------------------------ particle update
+    def kick(self, vel: torch.Tensor, acc: torch.Tensor, dt: float) -> None:
+        """v += a dt (in place)."""
+        vel, acc = self._check_vec3(vel, "vel"), self._check_vec3(acc, "acc")
+        N.check(self._lib.nf_kick(self._ctx, vel.data_ptr(), acc.data_ptr(), float(dt),
+                                  _stream_ptr(self.device)), self._ctx, "nf_kick")
+
+    def drift(self, pos: torch.Tensor, vel: torch.Tensor, dt: float) -> None:
+        """x += v dt, wrapped into the periodic box (in place)."""
+        pos, vel = self._check_vec3(pos, "pos"), self._check_vec3(vel, "vel")
+        N.check(self._lib.nf_drift(self._ctx, pos.data_ptr(), vel.data_ptr(), float(dt),
+                                   _stream_ptr(self.device)), self._ctx, "nf_drift")
+
+    def timestep(self, vel: torch.Tensor, acc: torch.Tensor, eta: float = 0.25) -> float:
+        """eta * min over cells of velocity dispersion / max |a| (Sec. 2.4)."""
+        vel, acc = self._check_vec3(vel, "vel"), self._check_vec3(acc, "acc")
+        out = ctypes.c_double()
+        N.check(self._lib.nf_timestep(self._ctx, vel.data_ptr(), acc.data_ptr(), float(eta),
+                                      ctypes.byref(out), _stream_ptr(self.device)), self._ctx,
+                "nf_timestep")
+        return out.value
+
+    def kdk_step(self, pos: torch.Tensor, vel: torch.Tensor, acc: torch.Tensor, dt: float, *,
+                 mass: torch.Tensor | None = None, gm=None, box_offsets=None) -> None:
+        """One kick-drift-kick leapfrog step in place; acc must hold the
+        accelerations of the binned positions and is updated."""
+        pos, vel, acc = (self._check_vec3(t, nm) for t, nm in ((pos, "pos"), (vel, "vel"), (acc, "acc")))
+        gm_scalar = 0.0
+        if mass is None:
+            if isinstance(gm, (list, tuple, np.ndarray)):
+                G = (ctypes.c_double * self.n_boxes)(*_as_list(gm, self.n_boxes, float))
+                N.check(self._lib.nf_set_box_masses(self._ctx, G), self._ctx, "nf_set_box_masses")
+            elif gm is not None:
+                N.check(self._lib.nf_set_box_masses(self._ctx, None), self._ctx, "nf_set_box_masses")
+                gm_scalar = float(gm)
+            else:
+                raise ValueError("give either mass or gm")
+        off = self._offsets(box_offsets)
+        offp = None if off is None else off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        rc = self._lib.nf_kdk_step(self._ctx, pos.data_ptr(), vel.data_ptr(), acc.data_ptr(),
+                                   None if mass is None else mass.data_ptr(), gm_scalar, float(dt),
+                                   offp, _stream_ptr(self.device))
+        N.check(rc, self._ctx, "nf_kdk_step")
+        self.generation += 1
+
     def accel_host(self, pos: np.ndarray, mass: np.ndarray | None = None, *, gm: float | None = None,
                    out: np.ndarray | None = None, box_offsets=None) -> np.ndarray:
         """End to end on host arrays: copy in, bin, compute, copy out (synchronous)."""
