@@ -303,12 +303,21 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
         const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
         const int S = 1 << log2s, G = 32 >> log2s;
         const int g = lane >> log2s, sp = lane & (S - 1);
-        const BoxDev B = a.boxes[box];
-        const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
-        const f2_t eps2 = f2_pack(B.eps2, B.eps2);
-        const f2_t c0 = f2_pack(B.sp_c0, B.sp_c0), c1 = f2_pack(B.sp_c1, B.sp_c1);
-        const f2_t c2 = f2_pack(B.sp_c2, B.sp_c2);
-        const f2_t kb0 = f2_pack(B.kb0, B.kb0), kb1 = f2_pack(B.kb1, B.kb1);
+        // box constants are read where they are used (not kept in registers
+        // across the tile loop)
+        const BoxDev *Bp = a.boxes + box;
+        const int nsrc = build_table(a, *Bp, w.cell, pfx, dlt, ofs);
+        const f2_t eps2 = f2_pack(Bp->eps2, Bp->eps2);
+        f2_t c0 = 0ull, c1 = 0ull, c2 = 0ull, kb0 = 0ull, kb1 = 0ull;
+        if (LAW == 1) {
+            c0 = f2_pack(Bp->sp_c0, Bp->sp_c0);
+            c1 = f2_pack(Bp->sp_c1, Bp->sp_c1);
+            c2 = f2_pack(Bp->sp_c2, Bp->sp_c2);
+        }
+        if (KDE) {
+            kb0 = f2_pack(Bp->kb0, Bp->kb0);
+            kb1 = f2_pack(Bp->kb1, Bp->kb1);
+        }
 
         f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K];
         f2_t lx[K], ly[K], lz[K], rho[K];
@@ -463,15 +472,15 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             const int si = g + G * k;
             if (sp == 0 && si < w.n) {
                 const int i = a.perm[w.first + si];
-                if (KDE) a.dens[i] = EQ ? dv * B.gm : dv;
+                if (KDE) a.dens[i] = EQ ? dv * __ldg(&Bp->gm) : dv;
                 if (a.out_f64) {
-                    const double sc = EQ ? B.gm_d * B.inv_h2_d : B.inv_h2_d;
+                    const double sc = EQ ? __ldg(&Bp->gm_d) * __ldg(&Bp->inv_h2_d) : __ldg(&Bp->inv_h2_d);
                     double *o = reinterpret_cast<double *>(a.out) + 3 * (int64_t)i;
                     o[0] = (double)v[0] * sc;
                     o[1] = (double)v[1] * sc;
                     o[2] = (double)v[2] * sc;
                 } else {
-                    const float sc = EQ ? B.gm * B.inv_h2 : B.inv_h2;
+                    const float sc = EQ ? __ldg(&Bp->gm) * __ldg(&Bp->inv_h2) : __ldg(&Bp->inv_h2);
                     float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
                     o[0] = v[0] * sc;
                     o[1] = v[1] * sc;
@@ -810,8 +819,8 @@ __global__ void k_gather_w(const float *__restrict__ w, int64_t n, const int *__
     }
 }
 
-// a10: FP64 momentum diagnostic, P = sum_i m_i a_i and sum_i m_i |a_i|,
-// two-level fixed-order reduction (deterministic).
+// a10: FP64 momentum diagnostic, P = sum_i m_i a_i (FP64 sums) and the scale
+// sum_i m_i |a_i|, two-level fixed-order reduction (deterministic).
 __global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sorted,
                                                   const int *__restrict__ perm, const void *acc,
                                                   int f64, int64_t n, double *partial) {
@@ -831,7 +840,10 @@ __global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sor
         s[0] += m * v[0];
         s[1] += m * v[1];
         s[2] += m * v[2];
-        s[3] += m * sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        // |a| only scales the check: an FP32 magnitude avoids an FP64 square
+        // root per particle (FP64 throughput is low on this GPU)
+        const float a2 = (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        s[3] += m * (double)sqrtf(a2);
     }
     __shared__ double red[8][4];
     for (int c = 0; c < 4; ++c) {

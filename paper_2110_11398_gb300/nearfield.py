@@ -8,6 +8,9 @@ device memory and the streams.
 from __future__ import annotations
 
 import ctypes
+import json
+import math
+import os
 from typing import Sequence
 
 import numpy as np
@@ -295,11 +298,58 @@ class NearField:
                         cur["use_graph"] if use_graph is None else int(use_graph))
         N.check(self._lib.nf_set_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_set_tuning")
 
-    def autotune(self, reps: int = 2) -> dict:
+    def autotune(self, reps: int = 2, cache: str | None = None) -> dict:
+        """Time the candidate launch shapes on the binned particles and keep
+        the fastest. With ``cache`` (a JSON file), a shape measured before for
+        the same device, problem kind, CPD and occupancy bucket is reused."""
+        key = None
+        if cache:
+            st = self.stats()
+            key = tuning_cache_key(torch.cuda.get_device_name(self.device), self.radius,
+                                   self.precision, self.softening, self.cpd, st["n_particles"],
+                                   st["n_cells"], st["max_occupancy"])
+            hit = load_tuning_cache(cache).get(key)
+            if hit:
+                self.set_tuning(**{k: hit[k] for k in ("sinks_per_lane", "warps_per_block",
+                                                       "blocks_per_sm") if k in hit})
+                return self.tuning
         t = N.nf_tuning()
         N.check(self._lib.nf_autotune(self._ctx, int(reps), ctypes.byref(t),
                                       _stream_ptr(self.device)), self._ctx, "nf_autotune")
+        if cache:
+            data = load_tuning_cache(cache)
+            data[key] = self.tuning
+            save_tuning_cache(cache, data)
         return self.tuning
+
+
+def tuning_cache_key(gpu: str, radius: int, precision: str, softening: str, cpd, n: int,
+                     n_cells: int, max_occupancy: int) -> str:
+    """Key of the autotuner cache: device, problem kind, CPD and a coarse
+    occupancy bucket (log2 of the mean and of the largest cell population)."""
+    mean = max(n, 1) / max(n_cells, 1)
+    b_mean = int(round(math.log2(max(mean, 1e-9))))
+    b_max = int(round(math.log2(max(max_occupancy, 1))))
+    cpds = "x".join(str(int(c)) for c in (cpd if isinstance(cpd, (list, tuple)) else [cpd]))
+    if len(cpds) > 64:
+        cpds = f"{len(cpd)}boxes"
+    return f"{gpu}|R{radius}|{precision}|{softening}|cpd{cpds}|mean{b_mean}|max{b_max}"
+
+
+def load_tuning_cache(path: str) -> dict:
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def save_tuning_cache(path: str, data: dict) -> None:
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class _NearFieldAccel(torch.autograd.Function):

@@ -320,15 +320,25 @@ def test_batched_per_box_masses_bit_identical_to_plain(dev):
     assert np.all(np.abs(np.array(mom["momentum"])) <= 1e-5 * mom["abs_momentum"])
 
 
-def test_autotune_picks_a_valid_shape(dev):
+def test_autotune_picks_a_valid_shape(dev, tmp_path):
+    import json
     box = synth.tiny()
     nf = make_nf(box, dev)
     nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
-    t = nf.autotune(reps=1)
+    cache = str(tmp_path / "tune.json")
+    t = nf.autotune(reps=1, cache=cache)
     assert t["sinks_per_lane"] in (1, 2, 4) and t["warps_per_block"] in (4, 8)
     ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
     assert_parity(nf.accel().cpu().numpy(), ref)
     nf.close()
+    # a second context reads the cached shape instead of timing again
+    (key, rec), = json.load(open(cache)).items()
+    rec["sinks_per_lane"] = 1 if t["sinks_per_lane"] != 1 else 2
+    json.dump({key: rec}, open(cache, "w"))
+    nf2 = make_nf(box, dev)
+    nf2.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    assert nf2.autotune(reps=1, cache=cache)["sinks_per_lane"] == rec["sinks_per_lane"]
+    nf2.close()
 
 
 def test_momentum_diagnostic(dev):
