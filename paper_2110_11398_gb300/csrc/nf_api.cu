@@ -261,9 +261,6 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     }
     if (n_cells >= ((int64_t)1 << 30))
         return fail(nullptr, NF_EINVAL, "nf_init: total cells must stay below 2^30");
-    if (nf::scan_tmp_ints(n_cells) > 8192 ||
-        nf::scan_tmp_ints(nf::radix_tiles(capacity) * 256) > 8192)
-        return fail(nullptr, NF_EINVAL, "nf_init: too many cells or particles for the scan");
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

@@ -297,21 +297,40 @@ int grid_for(int64_t n, int threads, int sm_count, int per_sm = 8) {
 
 }  // namespace
 
-// Exclusive scan of in[0..n) into out[0..n], out[n] = total. tmp holds
-// ceil(n / kScanTile) + 1 ints. Requires ceil(n / kScanTile) <= 8192.
+// Exclusive scan of in[0..n) into out[0..n], out[n] = total (in == out is
+// allowed). Block sums of 4096-element tiles go to tmp; up to 8192 of them
+// are scanned by one block, more by scanning the block sums recursively
+// (tmp holds scan_tmp_ints(n) ints).
 cudaError_t scan_exclusive(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s,
                            int64_t *launches) {
     if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    if (nb > kScanThreads * 8) return cudaErrorInvalidValue;
-    if (launches) *launches += 3;
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp);
-    k_scan_blocks<<<1, kScanThreads, 0, s>>>(tmp, (int)nb, out + n);
+    if (launches) *launches += 2;
+    if (nb <= kScanThreads * 8) {
+        k_scan_blocks<<<1, kScanThreads, 0, s>>>(tmp, (int)nb, out + n);
+        if (launches) *launches += 1;
+    } else {
+        // tmp[0..nb) scanned in place; its total lands in tmp[nb]
+        cudaError_t e = scan_exclusive(tmp, tmp, nb, tmp + nb + 1, s, launches);
+        if (e) return e;
+        e = cudaMemcpyAsync(out + n, tmp + nb, sizeof(int), cudaMemcpyDeviceToDevice, s);
+        if (e) return e;
+    }
     k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, tmp, out);
     return cudaGetLastError();
 }
 
-int64_t scan_tmp_ints(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+int64_t scan_tmp_ints(int64_t n) {
+    int64_t total = 0;
+    while (true) {
+        const int64_t nb = (n + kScanTile - 1) / kScanTile;
+        total += nb + 1;
+        if (nb <= kScanThreads * 8) break;
+        n = nb;
+    }
+    return total;
+}
 int64_t radix_tiles(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
 
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,

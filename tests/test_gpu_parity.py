@@ -181,6 +181,26 @@ def test_non_pow2_box_side(dev):
     assert_parity(got, ref)
 
 
+def test_large_cpd_multilevel_scan(dev):
+    """CPD = 400 gives 6.4e7 cells, more than one scan level covers: the cell
+    table must still be exact and the forces right."""
+    rng = np.random.default_rng(21)
+    n, cpd = 200000, 400
+    pos = rng.random((n, 3)).astype(np.float32)
+    box = synth.Box("cpd400", pos, 1.0, cpd, 0.1 / cpd, 1.0 / n)
+    nf = make_nf(box, dev)
+    nf.bin(torch.from_numpy(pos).to(dev), gm=box.gm)
+    cs, perm, _ = (t.cpu().numpy() for t in nf.binning())
+    acc = nf.accel().cpu().numpy()
+    nf.close()
+    ref = oracle.bin_particles(pos, 1.0, cpd)
+    assert np.array_equal(cs.astype(np.int64), ref["cell_start"])
+    assert np.array_equal(perm.astype(np.int64), ref["perm"])
+    idx = np.arange(0, n, 101)
+    ra = oracle.accel(pos, 1.0, cpd, 2, box.eps, m0=box.gm, sinks=idx, cid=ref["cid"])
+    assert_parity(acc[idx], ra, what="cpd400")
+
+
 def test_one_dense_cell_and_empty_cells(dev):
     """5000 particles in one cell of a CPD=9 box, plus a few elsewhere: the
     dense cell is split over many items; most cells are empty."""
