@@ -454,3 +454,64 @@ def test_adjoint_full_size_sampled(dev):
     idx, got, _ = _sampled(box, dev, 5000, 13, w=w)
     ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
     assert_parity(got, ref, what="adjoint 128^3")
+
+
+# ---------------------------------------------------------------- more edges
+def test_batched_with_an_empty_box(dev):
+    from paper_2110_11398_gb300 import NearField
+    boxes = synth.batched(n_boxes=3, lo_side=16, hi_side=24, seed0=30)
+    boxes[1].pos = boxes[1].pos[:0]                      # box 1 holds no particles
+    offs = np.cumsum([0] + [len(b.pos) for b in boxes])
+    nfb = NearField([b.L for b in boxes], [b.cpd for b in boxes], [b.eps for b in boxes],
+                    capacity=int(offs[-1]), device=dev)
+    pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+    nfb.bin(pos, gm=[b.gm for b in boxes], box_offsets=offs)
+    a = nfb.accel().cpu().numpy()
+    nfb.close()
+    for b, o0, o1 in zip(boxes, offs[:-1], offs[1:]):
+        if o1 > o0:
+            ref = oracle.accel(b.pos, b.L, b.cpd, b.R, b.eps, m0=b.gm)
+            assert_parity(a[o0:o1], ref, what=b.name)
+
+
+def test_argument_errors(dev):
+    from paper_2110_11398_gb300 import NFError, NearField
+    box = synth.tiny()
+    nf = NearField(box.L, box.cpd, box.eps, capacity=1000, device=dev)
+    with pytest.raises(NFError, match="NF_EINVAL"):          # beyond capacity
+        nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    nf.close()
+    nfb = NearField([1.0, 1.0], [9, 9], [1e-3, 1e-3], capacity=box.n, device=dev)
+    p = torch.from_numpy(box.pos).to(dev)
+    with pytest.raises(NFError, match="NF_EINVAL"):          # offsets must end at n
+        nfb.bin(p, gm=box.gm, box_offsets=[0, 100, 200])
+    with pytest.raises(NFError, match="NF_EINVAL"):          # and be non-decreasing
+        nfb.bin(p, gm=box.gm, box_offsets=[0, box.n + 1, box.n])
+    nfb.close()
+
+
+@pytest.mark.parametrize("R,cpd", [(1, 6), (3, 9)])
+def test_vjp_other_radii(dev, R, cpd):
+    rng = np.random.default_rng(R)
+    n = 6000
+    pos = rng.random((n, 3)).astype(np.float32)
+    box = synth.Box("r", pos, 1.0, cpd, 0.05 / cpd, 1.0 / n, R)
+    w = synth.cotangent(n, R)
+    ref = oracle.vjp(pos, w, 1.0, cpd, R, box.eps, m0=box.gm)
+    nf = make_nf(box, dev)
+    nf.bin(torch.from_numpy(pos).to(dev), gm=box.gm)
+    g = nf.vjp(torch.from_numpy(w).to(dev)).cpu().numpy()
+    nf.close()
+    assert_parity(g, ref, what=f"vjp R={R}")
+
+
+def test_fp64_vjp_unequal_masses(dev):
+    box = synth.tiny(seed=8)
+    mass = np.random.default_rng(9).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    w = synth.cotangent(box.n, 9)
+    ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    nf = make_nf(box, dev, "fp64")
+    nf.bin(torch.from_numpy(box.pos).to(dev), torch.from_numpy(mass).to(dev))
+    g = nf.vjp(torch.from_numpy(w).to(dev)).cpu().numpy()
+    nf.close()
+    assert np.median(frac_err(g, ref)) < 1e-7
