@@ -52,10 +52,8 @@ def dist_env():
 # dram__bytes_write.sum) from one ncu capture each, with the sha256 of the
 # kernel source they were taken on; a changed source reports null.
 TRAFFIC_CAPTURES = {
-    ("early_256c_cpd65", "k_pairs"): (5.301530e9 + 0.267132e9,
-                                      "82d4fb3106e4cf2966ab6156e136a1a6d236155b11952dbbb26e8b60d4d7522f"),
-    ("adjoint_128c_cpd33", "k_vjp"): (0.177744e9 + 0.035190e9,
-                                      "82d4fb3106e4cf2966ab6156e136a1a6d236155b11952dbbb26e8b60d4d7522f"),
+    ("early_256c_cpd65", "k_pairs"): (5.26e9 + 0.26691e9, "1adb8354156458dd336c04bab81f00b57e12ead3c4496e5abd2c90d42e8da52a"),
+    ("late_512c_cpd129", "k_pairs"): (57.17e9 + 2.67e9, "1adb8354156458dd336c04bab81f00b57e12ead3c4496e5abd2c90d42e8da52a"),
 }
 
 
