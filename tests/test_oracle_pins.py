@@ -325,3 +325,13 @@ def test_sink_subset_matches_full(oracle_mod):
     sub = np.array([0, 5, 77, box.n - 1, 1234])
     part = oracle_mod.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=sub)
     assert np.array_equal(part, full[sub])
+
+
+def test_golden_file_is_what_its_script_writes():
+    import os
+    import subprocess
+    import sys
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    out = subprocess.run([sys.executable, os.path.join(here, "make_two_body.py")],
+                         capture_output=True, text=True, check=True).stdout
+    assert out == open(os.path.join(here, "two_body.txt")).read()
