@@ -49,6 +49,30 @@ __device__ __forceinline__ int cell_index(double u, int cpd) {
     return c >= cpd ? cpd - 1 : c;
 }
 
+// The same cell and cell-relative coordinate in FP32 when L is a power of
+// two (FP64 is slow on this GPU). x*CPD = p + e exactly (e from an fma), and
+// scaling by 1/L = 2^-k is exact, so u = p + e. floor(u) is floor(p), less
+// one when p is an integer and e < 0. Then p - (c + 1/2) is exact (Sterbenz:
+// both within a factor of two) when c >= 1 or p >= 1/4, and adding e rounds
+// once: the result equals float32(u - (c + 1/2)) formed in double. Returns
+// false (the caller then uses the FP64 path) outside those conditions; they
+// also keep p >= 1/4, so e is never subnormal.
+__device__ __forceinline__ bool cell_rel_pow2(float x, float cpd_f, float inv_L, int cpd, int &c,
+                                              float &r) {
+    float p = x * cpd_f;
+    float e = fmaf(x, cpd_f, -p);
+    p *= inv_L;
+    e *= inv_L;
+    float fl = floorf(p);
+    int ci = (int)fl;
+    if (fl == p && e < 0.f) ci -= 1;
+    if (ci >= cpd) return false;
+    if (!(ci >= 1 || p >= 0.25f)) return false;
+    c = ci;
+    r = __fadd_rn(__fsub_rn(p, (float)ci + 0.5f), e);
+    return true;
+}
+
 // a1 + a2: cell id of every particle and per-cell counts.
 __global__ void k_cell_ids(const float *__restrict__ pos, int64_t n,
                            const int64_t *__restrict__ poff, int n_boxes,
@@ -67,10 +91,15 @@ __global__ void k_cell_ids(const float *__restrict__ pos, int64_t n,
             bool ok = true;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const double x = (double)pos[3 * i + a];
+                const float xf = pos[3 * i + a];
+                const double x = (double)xf;
                 const bool in = (x >= 0.0) && (x < B.L);   // false for NaN
                 ok = ok && in;
-                c3[a] = in ? cell_index(cell_unit(x, B, pow2 != 0), B.cpd) : 0;
+                int cc = 0;
+                float rr;
+                if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, (float)(1.0 / B.L), B.cpd, cc, rr)))
+                    cc = cell_index(cell_unit(x, B, pow2 != 0), B.cpd);
+                c3[a] = cc;
             }
             if (!ok) atomicOr(&st->error, 1);
             cell = B.cell_off + (c3[0] * B.cpd + c3[1]) * B.cpd + c3[2];
@@ -272,19 +301,29 @@ __global__ void k_gather(const float *__restrict__ pos, const float *__restrict_
         const int i = perm[k];
         const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
         const BoxDev B = boxes[b];
-        double r[3];
+        float rf[3];
+        double rd[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double x = (double)pos[3 * (int64_t)i + a];
+            const float xf = pos[3 * (int64_t)i + a];
+            const double x = (double)xf;
             const bool in = (x >= 0.0) && (x < B.L);
-            const double u = in ? cell_unit(x, B, pow2 != 0) : 0.5;
-            const int c = in ? cell_index(u, B.cpd) : 0;
-            r[a] = __dsub_rn(u, (double)c + 0.5);
+            int c;
+            float r32;
+            if (in && !sorted_d && pow2 &&
+                cell_rel_pow2(xf, (float)B.cpd, (float)(1.0 / B.L), B.cpd, c, r32)) {
+                rf[a] = r32;
+                rd[a] = (double)r32;
+            } else {
+                const double u = in ? cell_unit(x, B, pow2 != 0) : 0.5;
+                c = in ? cell_index(u, B.cpd) : 0;
+                rd[a] = __dsub_rn(u, (double)c + 0.5);
+                rf[a] = __double2float_rn(rd[a]);
+            }
         }
         const float m = mass ? mass[i] : B.gm;
-        sorted[k] = make_float4(__double2float_rn(r[0]), __double2float_rn(r[1]),
-                                __double2float_rn(r[2]), m);
-        if (sorted_d) sorted_d[k] = dbl4_make(r[0], r[1], r[2], (double)m);
+        sorted[k] = make_float4(rf[0], rf[1], rf[2], m);
+        if (sorted_d) sorted_d[k] = dbl4_make(rd[0], rd[1], rd[2], (double)m);
     }
 }
 

@@ -86,7 +86,8 @@ def test_binning_bit_exact_tiny(dev):
     _bin_case(synth.tiny(), dev)
 
 
-@pytest.mark.parametrize("L,cpd", [(1.0, 9), (3.7, 7), (250.0, 16), (1.0, 33)])
+@pytest.mark.parametrize("L,cpd", [(1.0, 9), (3.7, 7), (250.0, 16), (1.0, 33), (0.5, 13),
+                                   (2.0, 129), (1024.0, 65), (1.0, 1000)])
 def test_binning_bit_exact_faces_and_non_pow2_box(dev, L, cpd):
     rng = np.random.default_rng(cpd)
     x = rng.random((20000, 3)).astype(np.float32) * np.float32(L)
