@@ -260,13 +260,20 @@ def run_reference(args):
             sizes.append(m)
     value = tot_inter / tot_t
     name = f"batched_{len(boxes)}boxes" if args.workload == "batched" else boxes[0].name
+    if args.workload == "batched":
+        cfg = {"workload": name, "n": int(sum(b.n for b in boxes)), "boxes": len(boxes),
+               "n_per_box": [int(b.n) for b in boxes], "cpd_per_box": [int(b.cpd) for b in boxes],
+               "R": boxes[0].R}
+    else:
+        b0 = boxes[0]
+        cfg = {"workload": b0.name, "n": b0.n, "cpd": b0.cpd, "R": b0.R, "eps": b0.eps,
+               "softening": "plummer"}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "strong" if args.workload == "batched" else "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "n": int(sum(b.n for b in boxes)), "R": boxes[0].R,
-                   "cpd": boxes[0].cpd if len(boxes) == 1 else [b.cpd for b in boxes]},
+        "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                          "sample": f"{int(np.mean(sizes))} random sinks per step ({'VJP' if vjp else 'accelerations'}) "
                                    f"of the {name} workload"},
