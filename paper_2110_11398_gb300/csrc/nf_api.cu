@@ -293,6 +293,8 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         B.eps2 = (float)B.eps2_d;
         B.inv_h2 = (float)B.inv_h2_d;
         B.inv_h3 = (float)B.inv_h3_d;
+        B.Lf = (float)L;
+        B.inv_Lf = (float)(1.0 / L);
         if (softening == NF_SOFT_SPLINE) {
             // pair factor inside eps_s: (10 - 15 u + 6 u^2) / eps_s^3, u = r / eps_s,
             // as c0 + c1 r + c2 r^2 in cell units; s gets a 1e-30 floor instead of eps^2

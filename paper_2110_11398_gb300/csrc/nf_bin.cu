@@ -41,7 +41,7 @@ __device__ __forceinline__ int box_of_particle(const int64_t *poff, int n_boxes,
 // equals multiplication by 1/L, which avoids the FP64 divide.
 __device__ __forceinline__ double cell_unit(double x, const BoxDev &B, bool pow2) {
     double p = __dmul_rn(x, B.cpd_d);
-    return pow2 ? __dmul_rn(p, 1.0 / B.L) : __ddiv_rn(p, B.L);
+    return pow2 ? __dmul_rn(p, (double)B.inv_Lf) : __ddiv_rn(p, B.L);
 }
 
 __device__ __forceinline__ int cell_index(double u, int cpd) {
@@ -92,13 +92,15 @@ __global__ void k_cell_ids(const float *__restrict__ pos, int64_t n,
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const float xf = pos[3 * i + a];
-                const double x = (double)xf;
-                const bool in = (x >= 0.0) && (x < B.L);   // false for NaN
+                // range test (false for NaN); for a power-of-two L, L is a
+                // float and the test is exact in FP32
+                const bool in = pow2 ? (xf >= 0.f && xf < B.Lf)
+                                     : ((double)xf >= 0.0 && (double)xf < B.L);
                 ok = ok && in;
                 int cc = 0;
                 float rr;
-                if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, (float)(1.0 / B.L), B.cpd, cc, rr)))
-                    cc = cell_index(cell_unit(x, B, pow2 != 0), B.cpd);
+                if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, cc, rr)))
+                    cc = cell_index(cell_unit((double)xf, B, pow2 != 0), B.cpd);
                 c3[a] = cc;
             }
             if (!ok) atomicOr(&st->error, 1);
@@ -307,11 +309,10 @@ __global__ void k_gather(const float *__restrict__ pos, const float *__restrict_
         for (int a = 0; a < 3; ++a) {
             const float xf = pos[3 * (int64_t)i + a];
             const double x = (double)xf;
-            const bool in = (x >= 0.0) && (x < B.L);
+            const bool in = pow2 ? (xf >= 0.f && xf < B.Lf) : (x >= 0.0 && x < B.L);
             int c;
             float r32;
-            if (in && !sorted_d && pow2 &&
-                cell_rel_pow2(xf, (float)B.cpd, (float)(1.0 / B.L), B.cpd, c, r32)) {
+            if (in && !sorted_d && pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, c, r32)) {
                 rf[a] = r32;
                 rd[a] = (double)r32;
             } else {
@@ -562,6 +563,8 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
     B.inv_h3_d = 1.0 / (h * h * h);
     B.gm = (float)mass_if_null;
     B.gm_d = (double)B.gm;
+    B.Lf = (float)box_size;
+    B.inv_Lf = (float)(1.0 / box_size);
     int ex = 0;
     c.pow2_all = std::frexp(box_size, &ex) == 0.5 ? 1 : 0;
     const int64_t poff[2] = {0, n};

@@ -45,7 +45,9 @@ struct BoxDev {
     float sp_c0, sp_c1, sp_c2;   // spline law inside eps_s: f = c0 + c1 r + c2 r^2 (cell units)
     float kb0, kb1;    // density weight 1 - r^2/b^2 written as kb0 + kb1 s
     float gm;          // G m of every particle of this box when no mass array is given
-    double gm_d;       // same, double
+    float Lf;          // L as float (exact when L is a power of two)
+    float inv_Lf;      // 1 / L as float (exact when L is a power of two)
+    double gm_d;       // same G m, double
 };
 
 // One unit of pair work: `n` consecutive cell-sorted sinks of one cell,
