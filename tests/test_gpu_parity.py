@@ -516,3 +516,27 @@ def test_fp64_vjp_unequal_masses(dev):
     g = nf.vjp(torch.from_numpy(w).to(dev)).cpu().numpy()
     nf.close()
     assert np.median(frac_err(g, ref)) < 1e-7
+
+
+def test_batched_vjp_bit_identical_to_plain(dev):
+    """The adjoint over several boxes in one context equals each box's own
+    adjoint bit for bit, and the oracle on sampled sinks."""
+    from paper_2110_11398_gb300 import NearField
+    boxes = synth.batched(n_boxes=3, lo_side=16, hi_side=28, seed0=50)
+    offs = np.cumsum([0] + [b.n for b in boxes])
+    nfb = NearField([b.L for b in boxes], [b.cpd for b in boxes], [b.eps for b in boxes],
+                    capacity=int(offs[-1]), device=dev)
+    pos = torch.from_numpy(np.concatenate([b.pos for b in boxes])).to(dev)
+    w = torch.from_numpy(synth.cotangent(int(offs[-1]), 50)).to(dev)
+    nfb.bin(pos, gm=[b.gm for b in boxes], box_offsets=offs)
+    gb = nfb.vjp(w).cpu().numpy()
+    nfb.close()
+    for b, o0, o1 in zip(boxes, offs[:-1], offs[1:]):
+        nf = make_nf(b, dev)
+        nf.bin(pos[o0:o1].contiguous(), gm=b.gm)
+        gp = nf.vjp(w[o0:o1].contiguous()).cpu().numpy()
+        nf.close()
+        assert np.array_equal(gb[o0:o1].view(np.uint32), gp.view(np.uint32))
+        idx = np.arange(0, b.n, 11)
+        ref = oracle.vjp(b.pos, w[o0:o1].cpu().numpy(), b.L, b.cpd, b.R, b.eps, m0=b.gm, sinks=idx)
+        assert_parity(gp[idx], ref, what=f"batched vjp {b.name}")
