@@ -354,8 +354,12 @@ class PlainRunner:
             cfg["dt"] = self.dt
         return cfg
 
+    e2e_note = "nf_accel_host: H2D positions, bin, accelerations, D2H"
+
     def e2e(self, reps):
         torch = self.torch
+        if self.kdk:
+            return self._e2e_kdk(reps)
         hpos = torch.from_numpy(self.box.pos).pin_memory().numpy()
         hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory().numpy()
         self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
@@ -363,6 +367,33 @@ class PlainRunner:
         for _ in range(reps):
             self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
         return (time.perf_counter() - t0) / reps, int(hpos.nbytes), int(hacc.nbytes)
+
+    def _e2e_kdk(self, reps):
+        """One kick-drift-kick step on host state: positions, velocities and
+        accelerations go in from pinned memory and come back every step."""
+        torch = self.torch
+        self.e2e_note = "H2D positions, velocities, accelerations; kdk_step; D2H the same"
+        hx = self.pos.cpu().pin_memory()
+        hv = self.vel.cpu().pin_memory()
+        ha = self.out.cpu().pin_memory()
+        x, v, a = torch.empty_like(self.pos), torch.empty_like(self.vel), torch.empty_like(self.out)
+
+        def once():
+            x.copy_(hx, non_blocking=True)
+            v.copy_(hv, non_blocking=True)
+            a.copy_(ha, non_blocking=True)
+            self.nf.kdk_step(x, v, a, self.dt, gm=self.box.gm)
+            hx.copy_(x, non_blocking=True)
+            hv.copy_(v, non_blocking=True)
+            ha.copy_(a, non_blocking=True)
+            torch.cuda.synchronize()
+
+        once()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        nb = int(hx.nbytes + hv.nbytes + ha.nbytes)
+        return (time.perf_counter() - t0) / reps, nb, nb
 
     def oracle_check(self, seconds):
         torch = self.torch
@@ -419,6 +450,35 @@ class AdjointRunner(PlainRunner):
         self.fwd_ms.append(self.nf.stats()["pair_ms"])
         self.nf.vjp(self.w, out=self.grad)
 
+    e2e_note = "H2D positions and cotangent, bin, accelerations, VJP, D2H accelerations and gradient"
+
+    def e2e(self, reps):
+        """The adjoint step on host buffers: positions and cotangent in from
+        pinned memory, accelerations and gradient back, every step."""
+        torch = self.torch
+        hpos = torch.from_numpy(self.box.pos).pin_memory()
+        hw = torch.from_numpy(self.w_np).pin_memory()
+        hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory()
+        hgrad = torch.empty((self.n, 3), dtype=torch.float32).pin_memory()
+        pos, w = torch.empty_like(self.pos), torch.empty_like(self.w)
+
+        def once():
+            pos.copy_(hpos, non_blocking=True)
+            w.copy_(hw, non_blocking=True)
+            self.nf.bin(pos, gm=self.box.gm)
+            self.nf.accel(out=self.out)
+            self.nf.vjp(w, out=self.grad)
+            hacc.copy_(self.out, non_blocking=True)
+            hgrad.copy_(self.grad, non_blocking=True)
+            torch.cuda.synchronize()
+
+        once()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        return ((time.perf_counter() - t0) / reps, int(hpos.nbytes + hw.nbytes),
+                int(hacc.nbytes + hgrad.nbytes))
+
     def oracle_check(self, seconds):
         import oracle
         torch = self.torch
@@ -451,6 +511,7 @@ class BatchedRunner:
 
     kernel = "k_pairs"
     flops_per_pair = FLOPS_PER_PAIR
+    e2e_note = "nf_accel_host: H2D positions, bin, accelerations, D2H"
 
     def __init__(self, args, dev, rank=0, world=1):
         import torch
@@ -649,12 +710,10 @@ def run_ours(args):
     if not args.no_e2e:
         reps = max(1, min(args.steps, 3))
         dt, h2d, d2h = run.e2e(reps)
-        _, e2e_units = aggregate(0.0, interactions * run.passes if not isinstance(run, AdjointRunner)
-                                 else interactions, dist_or_none)
+        _, e2e_units = aggregate(0.0, interactions * run.passes, dist_or_none)
         dt_max, _ = aggregate(dt * 1e3, 0.0, dist_or_none)
         e2e = {"value": e2e_units / (dt_max / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": dt_max,
-               "note": "nf_accel_host: H2D positions, bin, accelerations, D2H"}
+               "d2h_bytes_per_step": d2h, "ms_per_step": dt_max, "note": run.e2e_note}
 
     cpu = None
     err = None
