@@ -176,6 +176,25 @@ def make_workload(name: str):
     return synth.make(name)
 
 
+def oracle_single_core_tiny():
+    """The oracle on one host core over the whole 32^3 tiny box (about 1.8e8
+    interactions, a second or two)."""
+    import oracle
+    box = make_workload("tiny")
+    nt = oracle.num_threads()
+    b = oracle.bin_particles(box.pos, box.L, box.cpd)
+    inter = oracle.interactions(b["cid"], box.cpd, box.R)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm, cid=b["cid"])
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(nt)
+    return {"value": inter / dt, "unit": UNIT, "cores": 1,
+            "sample": f"all {box.n} sinks of the {box.name} box ({inter:.3e} interactions, {dt:.1f} s)"}
+
+
 def oracle_sample(box, target_s: float, seed: int = 123):
     """Time the FP64 oracle on a random sink sample sized for ~target_s of
     CPU work; returns (interactions/s, sinks, interactions, seconds, idx, acc)."""
@@ -724,7 +743,7 @@ def run_ours(args):
         err = {"median": float(np.median(e)), "p99.9": float(np.quantile(e, 0.999)),
                "max": float(e.max()), "sinks": int(len(e))}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": sample}
+               "sample": sample, "single_core_tiny": oracle_single_core_tiny()}
 
     tuning = run.tuning()
     cfg = run.config()
