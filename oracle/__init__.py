@@ -56,6 +56,8 @@ def _load():
             lib.orc_accel.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, i64, vp]
             lib.orc_accel.restype = i32
             lib.orc_vjp.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, vp, vp, i64, vp]
+            lib.orc_vjp_ex.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, i32, vp, vp, i64, vp]
+            lib.orc_vjp_ex.restype = i32
             lib.orc_accel_ex.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, dbl, i32, dbl, vp, i64, vp, vp]
             lib.orc_accel_ex.restype = i32
             lib.orc_vjp.restype = i32
@@ -158,11 +160,13 @@ def accel_ex(pos, L: float, cpd: int, R: int, eps: float, *, law: str = "plummer
 
 
 def vjp(pos, w, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float = 1.0,
-        sinks=None, cid=None) -> np.ndarray:
+        sinks=None, cid=None, law: str = "plummer") -> np.ndarray:
     """Vector-Jacobian product d(sum_i w_i . a_i)/dx with the binning held fixed.
 
-    g_k = sum_j J(Delta_kj)(m_k w_j - m_j w_k), J = s^-3/2 I - 3 s^-5/2 D D^T
-    (derivative of the Plummer near-field sum of Sec. 3.1 / Sec. 5.2).
+    g_k = sum_j J(Delta_kj)(m_k w_j - m_j w_k) with J(D) = f I + (f'(r)/r) D D^T
+    for the pair law a = m D f(r): for Plummer J = s^-3/2 I - 3 s^-5/2 D D^T
+    (derivative of the near-field sum of Sec. 3.1 / Sec. 5.2); ``law="spline"``
+    differentiates the spline law of accel_ex, eps being its radius.
     """
     if cid is None:
         cid = bin_particles(np.asarray(pos, np.float32), L, cpd)["cid"]
@@ -171,9 +175,14 @@ def vjp(pos, w, L: float, cpd: int, R: int, eps: float, *, mass=None, m0: float 
     n = pos.shape[0]
     ns = n if sinks is None else sinks.shape[0]
     out = np.empty((ns, 3), np.float64)
-    _check(_load().orc_vjp(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L),
-                           int(cpd), int(R), float(eps), _ptr(w), _ptr(sinks), ns, _ptr(out)),
-           "orc_vjp")
+    if law == "plummer":
+        _check(_load().orc_vjp(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L),
+                               int(cpd), int(R), float(eps), _ptr(w), _ptr(sinks), ns, _ptr(out)),
+               "orc_vjp")
+    else:
+        _check(_load().orc_vjp_ex(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L),
+                                  int(cpd), int(R), float(eps), LAWS[law], _ptr(w), _ptr(sinks), ns,
+                                  _ptr(out)), "orc_vjp_ex")
     return out
 
 

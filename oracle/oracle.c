@@ -297,12 +297,32 @@ int orc_accel_ex(int64_t n, const double *pos, const int32_t *cid, const double 
  *     g_k = dLw/dx_k = sum_{j in nbr(k)} J(Delta_kj) (m_k w_j - m_j w_k).
  *   w [n*3] cotangent; g [ns*3] out; other arguments as orc_accel.
  */
+int orc_vjp_ex(int64_t n, const double *pos, const int32_t *cid, const double *mass,
+               double m0, double L, int cpd, int R, double eps, int law, const double *w,
+               const int64_t *sinks, int64_t ns, double *g);
+
 int orc_vjp(int64_t n, const double *pos, const int32_t *cid, const double *mass,
             double m0, double L, int cpd, int R, double eps, const double *w,
             const int64_t *sinks, int64_t ns, double *g)
 {
+    return orc_vjp_ex(n, pos, cid, mass, m0, L, cpd, R, eps, 0, w, sinks, ns, g);
+}
+
+/*
+ * orc_vjp_ex: orc_vjp for either pair law of orc_accel_ex. With
+ * P(D) = D f(r), r = |D|, the Jacobian is J(D) = f I + (f'(r)/r) D D^T:
+ *   law 0: f = s^(-3/2), f'/r = -3 s^(-5/2)           (s = r^2 + eps^2)
+ *   law 1, r >= eps: f = r^-3, f'/r = -3 r^-5
+ *   law 1, 0 < r < eps: f = (10 - 15u + 6u^2)/eps^3, f'(r) = (-15 + 12u)/eps^4
+ *   law 1, r = 0: J = f(0) I (the D D^T term vanishes as D -> 0).
+ * The spline's f and f' are continuous at r = eps, so J is too.
+ */
+int orc_vjp_ex(int64_t n, const double *pos, const int32_t *cid, const double *mass,
+               double m0, double L, int cpd, int R, double eps, int law, const double *w,
+               const int64_t *sinks, int64_t ns, double *g)
+{
     if (n < 0 || cpd < 1 || R < 0 || !(L > 0.0) || !(eps > 0.0)) return ORC_EINVAL;
-    if (2 * R + 1 > cpd) return ORC_EINVAL;
+    if (2 * R + 1 > cpd || law < 0 || law > 1) return ORC_EINVAL;
     int64_t ncell = (int64_t)cpd * cpd * cpd;
     int64_t *start, *list;
     int rc = build_lists(n, cid, ncell, &start, &list);
@@ -335,13 +355,33 @@ int orc_vjp(int64_t n, const double *pos, const int32_t *cid, const double *mass
                 double mj = mass ? mass[j] : m0;
                 double u[3];
                 for (int a = 0; a < 3; ++a) u[a] = mk * w[3 * j + a] - mj * w[3 * k + a];
-                double s32 = 1.0 / (s * sqrt(s));      /* s^(-3/2) */
-                double s52 = s32 / s;                   /* s^(-5/2) */
                 double Du = D[0] * u[0] + D[1] * u[1] + D[2] * u[2];
-                /* J u = s^(-3/2) u - 3 s^(-5/2) D (D . u) */
-                gx += s32 * u[0] - 3.0 * s52 * D[0] * Du;
-                gy += s32 * u[1] - 3.0 * s52 * D[1] * Du;
-                gz += s32 * u[2] - 3.0 * s52 * D[2] * Du;
+                if (law == 0) {
+                    double s32 = 1.0 / (s * sqrt(s));      /* s^(-3/2) */
+                    double s52 = s32 / s;                   /* s^(-5/2) */
+                    /* J u = s^(-3/2) u - 3 s^(-5/2) D (D . u) */
+                    gx += s32 * u[0] - 3.0 * s52 * D[0] * Du;
+                    gy += s32 * u[1] - 3.0 * s52 * D[1] * Du;
+                    gz += s32 * u[2] - 3.0 * s52 * D[2] * Du;
+                } else {
+                    double r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+                    double r = sqrt(r2), f, dfr;
+                    if (r >= eps) {
+                        f = 1.0 / (r2 * r);
+                        dfr = -3.0 * f / r2;
+                    } else if (r2 > 0.0) {
+                        double uu = r / eps;
+                        f = (10.0 - 15.0 * uu + 6.0 * uu * uu) / (eps2 * eps);
+                        dfr = (-15.0 + 12.0 * uu) / (eps2 * eps2 * r);
+                    } else {
+                        f = 10.0 / (eps2 * eps);
+                        dfr = 0.0;
+                    }
+                    /* J u = f u + (f'/r) D (D . u) */
+                    gx += f * u[0] + dfr * D[0] * Du;
+                    gy += f * u[1] + dfr * D[1] * Du;
+                    gz += f * u[2] + dfr * D[2] * Du;
+                }
             }
         }
         g[3 * q + 0] = gx;

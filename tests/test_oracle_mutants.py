@@ -5,7 +5,7 @@ Every mutant is a copy of oracle/oracle.c with one edit, compiled with gcc
 into a temporary library and swapped in for the real one while a set of
 independent checks runs (brute force over images, two-body closed form,
 Newton's third law, lattice symmetry, exact binning, finite differences of
-the adjoint). A mutant that passes every check would mean the pins cannot
+the Plummer and spline adjoints). A mutant that passes every check would mean the pins cannot
 see that mistake. CPU only.
 """
 import os
@@ -41,6 +41,10 @@ MUTANTS = {
                          "gx += s32 * u[0] - 1.0 * s52 * D[0] * Du;"),
     "vjp_sign": ("for (int a = 0; a < 3; ++a) u[a] = mk * w[3 * j + a] - mj * w[3 * k + a];",
                  "for (int a = 0; a < 3; ++a) u[a] = mj * w[3 * k + a] - mk * w[3 * j + a];"),
+    "vjp_spline_inner_slope": ("dfr = (-15.0 + 12.0 * uu) / (eps2 * eps2 * r);",
+                               "dfr = (-15.0 + 6.0 * uu) / (eps2 * eps2 * r);"),
+    "vjp_spline_outer_power": ("dfr = -3.0 * f / r2;", "dfr = -2.0 * f / r2;"),
+    "vjp_spline_sign": ("gx += f * u[0] + dfr * D[0] * Du;", "gx += f * u[0] - dfr * D[0] * Du;"),
 }
 
 
@@ -79,6 +83,7 @@ def _run_pins():
     """The pins of test_oracle_pins.py, evaluated without pytest; returns the
     list of pins that the current oracle library fails."""
     import test_oracle_pins as P
+    import test_oracle_spline_kde as S
     failed = []
     checks = [
         ("binning", lambda: P.test_binning_exact_containment_and_stability(oracle, 9, 1.0)),
@@ -89,6 +94,7 @@ def _run_pins():
         ("lattice", lambda: P.test_lattice_symmetry_zero(oracle)),
         ("newton", lambda: P.test_newton_third_law(oracle)),
         ("vjp_fd", lambda: P.test_vjp_two_body_finite_difference(oracle)),
+        ("vjp_spline_fd", lambda: S.test_spline_vjp_central_differences(oracle)),
     ]
     for nm, fn in checks:
         try:

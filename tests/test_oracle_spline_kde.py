@@ -129,3 +129,86 @@ def test_density_on_a_lattice(oracle_mod):
     _, rho = oracle_mod.accel_ex(pos, 1.0, cpd, 2, 0.1 * a, kde_b=1.2 * a, m0=2.0,
                                  cid=_cells(pos, 1.0, cpd))
     np.testing.assert_allclose(rho, 2.0 * (1 + 6 * (1 - 1 / 1.44)), rtol=1e-12)
+
+
+# ---------------------------------------------------------------- spline adjoint
+def test_spline_vjp_central_differences(oracle_mod):
+    """The spline adjoint against central differences of the forward spline
+    sum (binning frozen), with eps chosen so that both branches of the law
+    are common; translation leaves sum_i w_i . a_i unchanged, so the
+    gradient sums to zero."""
+    rng = np.random.default_rng(23)
+    cpd, L, R = 6, 1.0, 2
+    n = 250
+    pos = rng.random((n, 3))
+    mass = rng.uniform(0.5, 2.0, n)
+    spacing = L / n ** (1 / 3)
+    eps = 0.8 * spacing
+    cid = _cells(pos, L, cpd)
+    w = rng.standard_normal((n, 3))
+    g = oracle_mod.vjp(pos, w, L, cpd, R, eps, mass=mass, cid=cid, law="spline")
+
+    def lw(p):
+        return float((w * oracle_mod.accel_ex(p, L, cpd, R, eps, law="spline", mass=mass,
+                                              cid=cid)).sum())
+
+    h = 1e-5 * spacing
+    gscale = np.abs(g).max()
+    for k in rng.choice(n, 25, replace=False):
+        for a in range(3):
+            pp = pos.copy(); pp[k, a] += h
+            pm = pos.copy(); pm[k, a] -= h
+            fd = (lw(pp) - lw(pm)) / (2 * h)
+            assert abs(fd - g[k, a]) <= 2e-5 * gscale + 1e-6 * abs(g[k, a]), (k, a, fd, g[k, a])
+    assert np.abs(g.sum(0)).max() <= 1e-12 * np.abs(g).sum()
+
+
+def test_spline_vjp_two_body_symbolic(oracle_mod):
+    """Two bodies, inside and outside the spline radius and across a periodic
+    face: the adjoint equals the Jacobian of the pair force obtained by
+    symbolic differentiation of F(r) = r (10 - 15u + 6u^2)/eps^3 (u < 1) and
+    1/r^2 (u >= 1), the law the forward pins fix."""
+    sp = pytest.importorskip("sympy")
+    L, cpd, R, eps = 1.0, 5, 2, 0.02
+    x, y, z, e = sp.symbols("x y z e", positive=True)
+    r = sp.sqrt(x * x + y * y + z * z)
+    u = r / e
+    inside = sp.Matrix([x, y, z]) * (10 - 15 * u + 6 * u * u) / e ** 3
+    outside = sp.Matrix([x, y, z]) / r ** 3
+    J_in = sp.lambdify((x, y, z, e), inside.jacobian([x, y, z]), "numpy")
+    J_out = sp.lambdify((x, y, z, e), outside.jacobian([x, y, z]), "numpy")
+    rng = np.random.default_rng(8)
+    for dist in (0.004, 0.013, 0.0199, 0.0201, 0.05):
+        d = rng.standard_normal(3); d *= dist / np.linalg.norm(d)
+        a = np.array([0.001, 0.5, 0.5])
+        b = np.mod(a + d, L)
+        pos = np.stack([a, b])
+        m = np.array([1.3, 0.4])
+        w = rng.standard_normal((2, 3))
+        g = oracle_mod.vjp(pos, w, L, cpd, R, eps, mass=m, cid=_cells(pos, L, cpd), law="spline")
+        J = np.array((J_in if dist < eps else J_out)(*d, eps), dtype=np.float64)   # J(D_01) = J(D_10)
+        g0 = J @ (m[0] * w[1] - m[1] * w[0])
+        np.testing.assert_allclose(g[0], g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+        np.testing.assert_allclose(g[1], -g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+
+
+def test_spline_vjp_coincident_bodies(oracle_mod):
+    """At r = 0 the pair Jacobian is f(0) I = (10/eps^3) I: the D D^T term
+    vanishes with D."""
+    L, cpd, R, eps = 1.0, 5, 2, 0.02
+    pos = np.array([[0.3, 0.3, 0.3], [0.3, 0.3, 0.3]])
+    m = np.array([2.0, 0.5])
+    w = np.array([[1.0, -2.0, 0.5], [0.25, 3.0, -1.0]])
+    g = oracle_mod.vjp(pos, w, L, cpd, R, eps, mass=m, cid=_cells(pos, L, cpd), law="spline")
+    g0 = 10.0 / eps ** 3 * (m[0] * w[1] - m[1] * w[0])
+    np.testing.assert_allclose(g[0], g0, rtol=1e-13)
+    np.testing.assert_allclose(g[1], -g0, rtol=1e-13)
+
+
+def test_plummer_vjp_unchanged_by_the_law_switch(oracle_mod):
+    box = synth.tiny()
+    w = synth.cotangent(box.n, 3)
+    idx = np.arange(0, box.n, 97)
+    a = oracle_mod.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
+    b = oracle_mod.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, law="plummer")
+    assert np.array_equal(a, b)
