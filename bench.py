@@ -36,6 +36,7 @@ FLOPS_PER_PAIR = 20          # Plummer pair: 3 sub, 3 fma, rsqrt (2), 3 mul (r^3
 SPLINE_EXTRA_FLOPS = 6       # r = s rsqrt(s), two fma for the polynomial, min
 KDE_EXTRA_FLOPS = 4          # fma for 1 - r^2/b^2, max with 0, add
 VJP_FLOPS_PER_PAIR = 45      # adjoint pair (see the design notes)
+SPLINE_VJP_EXTRA_FLOPS = 8   # r = s rsqrt(s), two fma for the polynomial, fma for f'/r, min
 METRIC = "near-field pair interactions/s"
 UNIT = "interactions/s"
 
@@ -461,7 +462,7 @@ class AdjointRunner(PlainRunner):
         self.grad = self.torch.empty((self.n, 3), dtype=self.torch.float32, device=dev)
         self.passes = 2
         self.fwd_ms = []
-        self.flops_per_pair = VJP_FLOPS_PER_PAIR
+        self.flops_per_pair = VJP_FLOPS_PER_PAIR + (SPLINE_VJP_EXTRA_FLOPS if self.law == "spline" else 0)
 
     def step(self):
         self.nf.bin(self.pos, gm=self.box.gm)
@@ -507,15 +508,16 @@ class AdjointRunner(PlainRunner):
         order = rng.permutation(self.n)
         pos64 = self.box.pos.astype(np.float64)
         k = 2048
+        eps = 2.5 * self.box.eps if self.law == "spline" else self.box.eps
         t0 = time.perf_counter()
-        oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, self.box.eps,
-                   m0=self.box.gm, sinks=order[:k], cid=b["cid"])
+        oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, eps,
+                   m0=self.box.gm, sinks=order[:k], cid=b["cid"], law=self.law)
         rate = nsrc[order[:k]].sum() / max(time.perf_counter() - t0, 1e-4)
         m = max(k, min(self.n, int(np.searchsorted(np.cumsum(nsrc[order]), rate * seconds)) + 1))
         idx = np.sort(order[:m])
         t0 = time.perf_counter()
-        ref = oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, self.box.eps,
-                         m0=self.box.gm, sinks=idx, cid=b["cid"])
+        ref = oracle.vjp(pos64, self.w_np, self.box.L, self.box.cpd, self.box.R, eps,
+                         m0=self.box.gm, sinks=idx, cid=b["cid"], law=self.law)
         dt = time.perf_counter() - t0
         got = self.grad[torch.from_numpy(idx).to(self.grad.device)].double().cpu().numpy()
         sample = (f"VJP on {m} random sinks ({int(nsrc[idx].sum()):.3e} interactions, {dt:.1f} s) "

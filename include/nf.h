@@ -183,8 +183,13 @@ NF_API int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, con
  * nf_compute_accel_vjp -- vector-Jacobian product of the accelerations with
  * respect to the positions, for the scalar sum_i w_i . a_i with the binning of
  * the last nf_bin_particles held fixed:
- *     g_k = sum_{j near k} J(D_kj) (m_k w_j - m_j w_k),
- *     J(D) = s^(-3/2) I - 3 s^(-5/2) D D^T,  s = |D|^2 + eps^2,  D_kj = x_j - x_k.
+ *     g_k = sum_{j near k} J(D_kj) (m_k w_j - m_j w_k),  D_kj = x_j - x_k,
+ * with J(D) = f I + (f'(r)/r) D D^T the Jacobian of the pair term D f(r):
+ *     NF_SOFT_PLUMMER: J(D) = s^(-3/2) I - 3 s^(-5/2) D D^T,  s = |D|^2 + eps^2;
+ *     NF_SOFT_SPLINE:  f = (10 - 15u + 6u^2)/eps_s^3 with f'(r) = (-15 + 12u)/eps_s^4
+ *                      for u = r/eps_s < 1, else f = r^-3, f'/r = -3 r^-5
+ *                      (no counterpart in the paper, which does not use the
+ *                      adjoint; the derivative of its near-field sum, Sec. 3.1).
  * Pair terms are recomputed, not stored.
  *   w         device [N x 3] float32 cotangent, input order
  *   grad_pos  device [N x 3] float32 out, input order, caller-owned

@@ -302,6 +302,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
             B.sp_c0 = (float)(10.0 / (e * e * e));
             B.sp_c1 = (float)(-15.0 / (e * e * e * e));
             B.sp_c2 = (float)(6.0 / (e * e * e * e * e));
+            B.sp_eps = (float)e;
             B.eps2_d = 0.0;
             B.eps2 = 1e-30f;
         }
@@ -499,8 +500,6 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_vjp: no binned particles");
-    if (c->softening != NF_SOFT_PLUMMER)
-        return fail(c, NF_EINVAL, "nf_compute_accel_vjp: the adjoint is implemented for the Plummer law");
     if (c->n > 0 && (!w || !grad_pos)) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: w and grad_pos are required");
     int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
     if (rc) return rc;

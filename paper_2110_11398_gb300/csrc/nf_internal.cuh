@@ -43,6 +43,7 @@ struct BoxDev {
     float inv_h2;      // 1 / h^2, FP32
     float inv_h3;      // 1 / h^3, FP32
     float sp_c0, sp_c1, sp_c2;   // spline law inside eps_s: f = c0 + c1 r + c2 r^2 (cell units)
+    float sp_eps;                // eps_s in cell units (branch test of the spline adjoint)
     float kb0, kb1;    // density weight 1 - r^2/b^2 written as kb0 + kb1 s
     float gm;          // G m of every particle of this box when no mass array is given
     float Lf;          // L as float (exact when L is a power of two)

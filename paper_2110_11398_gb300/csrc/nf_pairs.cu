@@ -563,12 +563,22 @@ __global__ void __launch_bounds__(512) k_pairs_f64(PairArgs a) {
 }
 
 // Adjoint (vector-Jacobian product) pair kernel:
-//   g_k = sum_j J(D)(m_k w_j - m_j w_k),  J(D) u = s^-3/2 u - 3 s^-5/2 D (D.u).
+//   g_k = sum_j J(D)(m_k w_j - m_j w_k),  J(D) u = f u + (f'(r)/r) D (D.u)
+// for the pair law a = m D f(r).
+// LAW 0 (Plummer): f = s^-3/2, f'/r = -3 s^-5/2.
+// LAW 1 (spline): f = c0 + c1 r + c2 r^2 and f'/r = c1/r + 2 c2 for
+//   r < eps_s, else f = r^-3 and f'/r = -3 r^-5. The branch is chosen by
+//   comparing r with eps_s, not the two values as in the forward kernel:
+//   the law is C^2 at eps_s, so near it the values agree to rounding and
+//   either choice gives the same force, but the slopes f' differ at first
+//   order in (r - eps_s)^2 and the wrong branch would show in J. At the self
+//   pair (s at its 1e-30 floor) the polynomial branch is taken and every
+//   factor is finite; u = 0 there, so the term is 0.
 // Each pair's whole J u goes into one accumulator: the two parts of J u grow
 // coherently over j (the -m_j w_k term points the same way for every j) and
 // only cancel in their sum, so accumulating them apart loses precision.
 // Sums are blocked per tile like the forward kernel.
-template <int K, bool EQ>
+template <int K, bool EQ, int LAW = 0>
 __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -593,6 +603,15 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
         const BoxDev B = a.boxes[box];
         const int nsrc = build_table(a, B, w.cell, pfx, dlt, ofs);
         const f2_t eps2 = f2_pack(B.eps2, B.eps2);
+        f2_t c0 = 0ull, c1 = 0ull, c2 = 0ull, c2x2 = 0ull;
+        float e_s = 0.f;
+        if (LAW == 1) {
+            c0 = f2_pack(B.sp_c0, B.sp_c0);
+            c1 = f2_pack(B.sp_c1, B.sp_c1);
+            c2 = f2_pack(B.sp_c2, B.sp_c2);
+            c2x2 = f2_pack(2.f * B.sp_c2, 2.f * B.sp_c2);
+            e_s = B.sp_eps;
+        }
 
         f2_t xi[K], yi[K], zi[K], wxi[K], wyi[K], wzi[K], mi[K];
         f2_t gx[K], gy[K], gz[K];
@@ -691,10 +710,27 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
                     f2_t du = f2_mul(dx, ux);
                     du = f2_fma(dy, uy, du);
                     du = f2_fma(dz, uz, du);
-                    const f2_t c = f2_mul(f2_mul(du, r5), minus3);
-                    tx[k] = f2_fma(c, dx, f2_fma(r3, ux, tx[k]));
-                    ty[k] = f2_fma(c, dy, f2_fma(r3, uy, ty[k]));
-                    tz[k] = f2_fma(c, dz, f2_fma(r3, uz, tz[k]));
+                    f2_t c, f = r3;
+                    if (LAW == 0) {
+                        c = f2_mul(f2_mul(du, r5), minus3);
+                    } else {
+                        const f2_t rr = f2_mul(s, r);
+                        const f2_t poly = f2_fma(f2_fma(c2, rr, c1), rr, c0);
+                        const f2_t dpoly = f2_fma(c1, r, c2x2);
+                        const f2_t dout = f2_mul(r5, minus3);
+                        float p0, p1, q0, q1, d0, d1, e0, e1, r0, r1;
+                        f2_unpack(poly, p0, p1);
+                        f2_unpack(r3, q0, q1);
+                        f2_unpack(dpoly, d0, d1);
+                        f2_unpack(dout, e0, e1);
+                        f2_unpack(rr, r0, r1);
+                        const bool in0 = r0 < e_s, in1 = r1 < e_s;
+                        f = f2_pack(in0 ? p0 : q0, in1 ? p1 : q1);
+                        c = f2_mul(du, f2_pack(in0 ? d0 : e0, in1 ? d1 : e1));
+                    }
+                    tx[k] = f2_fma(c, dx, f2_fma(f, ux, tx[k]));
+                    ty[k] = f2_fma(c, dy, f2_fma(f, uy, ty[k]));
+                    tz[k] = f2_fma(c, dz, f2_fma(f, uz, tz[k]));
                 }
             }
 #pragma unroll
@@ -898,11 +934,17 @@ void *pair_kernel(int prec, int K, int eq, int law = 0, int kde = 0) {
     return nullptr;
 }
 
-void *vjp_kernel(int prec, int K, int eq) {
-    if (prec == NF_PREC_FP64_REF) return fptr(k_vjp_f64);
-    if (K == 1) return eq ? fptr(k_vjp<1, true>) : fptr(k_vjp<1, false>);
-    if (K == 2) return eq ? fptr(k_vjp<2, true>) : fptr(k_vjp<2, false>);
-    if (K == 4) return eq ? fptr(k_vjp<4, true>) : fptr(k_vjp<4, false>);
+void *vjp_kernel(int prec, int K, int eq, int law) {
+    if (prec == NF_PREC_FP64_REF) return law == 0 ? fptr(k_vjp_f64) : nullptr;
+#define NF_SELV(KK)                                                                    \
+    if (K == KK) {                                                                     \
+        if (law == 1) return eq ? fptr(k_vjp<KK, true, 1>) : fptr(k_vjp<KK, false, 1>); \
+        return eq ? fptr(k_vjp<KK, true>) : fptr(k_vjp<KK, false>);                     \
+    }
+    NF_SELV(1)
+    NF_SELV(2)
+    NF_SELV(4)
+#undef NF_SELV
     return nullptr;
 }
 
@@ -1050,7 +1092,7 @@ cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, 
         if (e) return e;
     }
     const int K = c->precision == NF_PREC_FP64_REF ? 1 : t.sinks_per_lane;
-    void *fn = vjp_kernel(c->precision, K, c->equal_mass);
+    void *fn = vjp_kernel(c->precision, K, c->equal_mass, c->softening == NF_SOFT_SPLINE ? 1 : 0);
     if (!fn) return cudaErrorInvalidValue;
     return launch_generic(c, fn, 1, make_args(c, grad, 0), t, s);
 }
