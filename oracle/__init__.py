@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "farfield.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -33,12 +34,13 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` with gcc (-O2, OpenMP, no FMA contraction)."""
+    """Compile ``oracle.c`` and ``farfield.c`` with gcc (-O2, OpenMP, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or \
+            os.path.getmtime(_LIB) < max(os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC",
-               "-shared", _SRC, "-o", tmp, "-lm"]
+               "-shared", *_SRCS, "-o", tmp, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -65,6 +67,14 @@ def _load():
             lib.orc_cell_timestep.restype = dbl
             lib.orc_interactions.argtypes = [i64, vp, i32, i32, vp]
             lib.orc_interactions.restype = i64
+            lib.orc_far_dtensor.argtypes = [vp, i32, i32, dbl, i32, vp]
+            lib.orc_far_dtensor.restype = i32
+            lib.orc_far_multi_indices.argtypes = [i32, vp]
+            lib.orc_far_multi_indices.restype = i32
+            lib.orc_ewald_accel.argtypes = [i64, vp, vp, dbl, dbl, dbl, vp]
+            lib.orc_ewald_accel.restype = i32
+            lib.orc_far_accel.argtypes = [i64, vp, vp, vp, dbl, dbl, i32, i32, i32, dbl, vp]
+            lib.orc_far_accel.restype = i32
             lib.orc_num_threads.argtypes = []
             lib.orc_num_threads.restype = i32
             lib.orc_set_num_threads.argtypes = [i32]
@@ -236,3 +246,57 @@ def kdk_step(pos32, vel32, dt: float, L: float, cpd: int, R: int, eps: float, *,
     a1 = accel(x1, L, cpd, R, eps, m0=m0)
     v1 = (v_half.astype(np.float64) + 0.5 * dt * a1).astype(np.float32)
     return x1, v1, a1
+
+
+# ---------------------------------------------------------------- far field
+def far_multi_indices(Q: int) -> np.ndarray:
+    """The (a, b, c) multi-indices with a + b + c <= Q in the far-field
+    oracle's order (total degree, then a, then b descending)."""
+    n = (Q + 1) * (Q + 2) * (Q + 3) // 6
+    out = np.empty((n, 3), np.int32)
+    _check(_load().orc_far_multi_indices(int(Q), _ptr(out)), "orc_far_multi_indices")
+    return out
+
+
+def far_dtensor(d, P: int, R: int, alpha: float, Q: int) -> np.ndarray:
+    """Ewald sum of the Cartesian derivatives d^q of the periodic 1/r at the
+    point ``d`` (cell units, period P), |q| <= Q (order of far_multi_indices);
+    with R >= 0 the near-field image of an integer offset is left out (the
+    derivatives tensor of Sec. 3.1), with R = -1 nothing is."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = (Q + 1) * (Q + 2) * (Q + 3) // 6
+    out = np.empty(n, np.float64)
+    _check(_load().orc_far_dtensor(_ptr(d), int(P), int(R), float(alpha), int(Q), _ptr(out)),
+           "orc_far_dtensor")
+    return out
+
+
+def ewald_accel(pos, L: float, *, mass=None, m0: float = 1.0, alpha: float | None = None) -> np.ndarray:
+    """Total periodic acceleration (Ewald sum, uniform background): near plus
+    far field, unsoftened. ``alpha`` in 1/box units (default 3.5 / L)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    if mass is not None:
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+    out = np.empty((n, 3), np.float64)
+    _check(_load().orc_ewald_accel(n, _ptr(pos), _ptr(mass), float(m0), float(L),
+                                   float(alpha or 3.5 / L), _ptr(out)), "orc_ewald_accel")
+    return out
+
+
+def far_accel(pos, L: float, cpd: int, R: int, p: int = 8, *, mass=None, m0: float = 1.0,
+              cid=None, alpha: float | None = None) -> np.ndarray:
+    """Far-field acceleration by cell multipoles, the periodic derivatives
+    tensor and Taylor series of order p (Sec. 3.1). ``alpha`` in 1/cell units
+    (default 3.5 / CPD)."""
+    if cid is None:
+        cid = bin_particles(np.asarray(pos, np.float32), L, cpd)["cid"]
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    cid = np.ascontiguousarray(cid, dtype=np.int32)
+    n = pos.shape[0]
+    if mass is not None:
+        mass = np.ascontiguousarray(mass, dtype=np.float64)
+    out = np.empty((n, 3), np.float64)
+    _check(_load().orc_far_accel(n, _ptr(pos), _ptr(cid), _ptr(mass), float(m0), float(L), int(cpd),
+                                 int(R), int(p), float(alpha or 3.5 / cpd), _ptr(out)), "orc_far_accel")
+    return out

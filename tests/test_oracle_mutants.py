@@ -5,7 +5,8 @@ Every mutant is a copy of oracle/oracle.c with one edit, compiled with gcc
 into a temporary library and swapped in for the real one while a set of
 independent checks runs (brute force over images, two-body closed form,
 Newton's third law, lattice symmetry, exact binning, finite differences of
-the Plummer and spline adjoints). A mutant that passes every check would mean the pins cannot
+the Plummer and spline adjoints, the lattice constant of the far-field
+tensor, far + near against the Ewald sum). A mutant that passes every check would mean the pins cannot
 see that mistake. CPU only.
 """
 import os
@@ -16,6 +17,7 @@ import pytest
 import oracle
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+FAR = os.path.join(os.path.dirname(oracle.__file__), "farfield.c")
 
 MUTANTS = {
     "drop_eps2": ("double s = ddx * ddx + ddy * ddy + ddz * ddz + eps2;",
@@ -45,19 +47,35 @@ MUTANTS = {
                                "dfr = (-15.0 + 6.0 * uu) / (eps2 * eps2 * r);"),
     "vjp_spline_outer_power": ("dfr = -3.0 * f / r2;", "dfr = -2.0 * f / r2;"),
     "vjp_spline_sign": ("gx += f * u[0] + dfr * D[0] * Du;", "gx += f * u[0] - dfr * D[0] * Du;"),
+    # far field (farfield.c)
+    "far_multipole_sign": ("coef[m] = (((a + b + c) & 1) ? -1.0 : 1.0) /", "coef[m] = 1.0 /"),
+    "far_offset_direction": ("const int64_t e = ((int64_t)((cx - x2 + cpd) % cpd) * cpd",
+                             "const int64_t e = ((int64_t)((x2 - cx + cpd) % cpd) * cpd"),
+    "far_taylor_factorial": ("const double yj = pow(y[0], ja) * pow(y[1], jb) * pow(y[2], jc) /\n                                  (factorial(ja) * factorial(jb) * factorial(jc));",
+                             "const double yj = pow(y[0], ja) * pow(y[1], jb) * pow(y[2], jc) /\n                                  (factorial(ja) * factorial(jb));"),
+    "far_recip_phase": ("case 1: re = -sn; break;", "case 1: re = sn; break;"),
+    "far_no_background": ("out[0] -= M_PI / (alpha * alpha * V);", "out[0] -= 0.0;"),
+    "far_near_image_kept": ("            g_minus_erf(r, alpha, Q, g);\n        } else {",
+                            "            g_minus_erf(r, alpha, Q, g);\n            for (int jj = 0; jj <= Q; ++jj) g[jj] *= 0.5;\n        } else {"),
 }
 
 
 def _build(name, tmp):
-    src = open(SRC).read()
     old, new = MUTANTS[name]
-    assert src.count(old) >= 1, name
-    src = src.replace(old, new, 1)
-    c = tmp / f"{name}.c"
+    files = []
+    hits = 0
+    for path in (SRC, FAR):
+        src = open(path).read()
+        if old in src:
+            src = src.replace(old, new, 1)
+            hits += 1
+        c = tmp / f"{name}_{os.path.basename(path)}"
+        c.write_text(src)
+        files.append(str(c))
+    assert hits == 1, name
     so = tmp / f"{name}.so"
-    c.write_text(src)
-    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", str(c),
-                    "-o", str(so), "-lm"], check=True)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                    *files, "-o", str(so), "-lm"], check=True)
     return str(so)
 
 
@@ -71,7 +89,7 @@ def test_mutant_is_caught(name, tmp_path):
         # keep oracle.build() from recompiling over the mutant
         orig_build = oracle.build
         oracle.build = lambda force=False: so
-        failed = _run_pins()
+        failed = _run_pins(first_only=True)
     finally:
         oracle.build = orig_build
         oracle._lib = saved_lib
@@ -79,11 +97,13 @@ def test_mutant_is_caught(name, tmp_path):
     assert failed, f"mutant {name} passed every pin"
 
 
-def _run_pins():
-    """The pins of test_oracle_pins.py, evaluated without pytest; returns the
-    list of pins that the current oracle library fails."""
+def _run_pins(first_only=False):
+    """The pins of test_oracle_pins.py (and of the spline and far-field pin
+    files), evaluated without pytest; returns the list of pins that the
+    current oracle library fails (only the first with ``first_only``)."""
     import test_oracle_pins as P
     import test_oracle_spline_kde as S
+    import test_oracle_farfield as F
     failed = []
     checks = [
         ("binning", lambda: P.test_binning_exact_containment_and_stability(oracle, 9, 1.0)),
@@ -95,12 +115,17 @@ def _run_pins():
         ("newton", lambda: P.test_newton_third_law(oracle)),
         ("vjp_fd", lambda: P.test_vjp_two_body_finite_difference(oracle)),
         ("vjp_spline_fd", lambda: S.test_spline_vjp_central_differences(oracle)),
+        ("far_lattice_constant", lambda: F.test_tensor_origin_value_is_the_cubic_lattice_constant(5)),
+        ("far_vs_ewald", F.test_far_plus_near_equals_ewald_and_converges_with_order),
+        ("far_cell_shift", F.test_far_field_follows_a_whole_cell_shift),
     ]
     for nm, fn in checks:
         try:
             fn()
         except Exception:
             failed.append(nm)
+            if first_only:
+                break
     return failed
 
 
