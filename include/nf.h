@@ -199,6 +199,39 @@ NF_API int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, con
 NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream);
 
 /*
+ * nf_far_init -- enables the far field of the near/far split for a one-box
+ * context (Sec. 3.1: Taylor series of order p about every cell centre, their
+ * coefficients the cyclic convolution, done in Fourier space, of the cells'
+ * multipole moments with the derivatives tensor of the periodic Green's
+ * function). Builds that tensor once, for the context's CPD and near-field
+ * radius R, with every image in the near field left out:
+ *     D_q(d) = sum_n d^q (1/r) at d + n CPD, d + n CPD not in [-R, R]^3,
+ * |q| <= 2p, as an Ewald sum with a uniform background (forces from density
+ * fluctuations, the periodic convention of cosmological codes).
+ *   order   p in [1, 8] (the paper uses 8)
+ * Allocates about 16 (p + 1)(p + 2)(p + 3)(2p + 1)(2p + 2)(2p + 3) / 36 CPD^3
+ * bytes for the transformed tensor (17 GB at p = 8, CPD = 129) plus as much
+ * again while it is built. Synchronous.
+ * Returns NF_OK, NF_EINVAL (order, CPD > 192, several boxes), NF_ENOMEM or
+ * NF_ECUDA (cuFFT errors included).
+ */
+NF_API int nf_far_init(nf_ctx *ctx, int order, void *stream);
+
+/*
+ * nf_compute_far -- far-field accelerations of the binned particles:
+ * multipoles M_m(c) = sum_j G m_j z_j^m (z relative to the cell centre, cell
+ * units, |m| <= p), their transform, T_k = sum_m (-1)^|m| / m! D_{k+m} M_m per
+ * frequency, the inverse transform, and a = grad sum_k T_k y^k / k! at each
+ * particle, scaled to box units. The Plummer or spline softening of the near
+ * field does not enter: the far field is unsoftened.
+ *   acc         device [N x 3] float32, input order; written, or with
+ *               accumulate != 0 added to (e.g. onto the near field)
+ * Returns NF_OK, NF_ESTATE (no nf_far_init or no binning), NF_EINVAL or
+ * NF_ECUDA. Asynchronous.
+ */
+NF_API int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream);
+
+/*
  * Particle update with a global timestep (Sec. 2.4: second-order leapfrog,
  * kick-drift-kick). All arrays are device [N x 3] float32 in input order, N
  * and the box of each particle being those of the last nf_bin_particles.

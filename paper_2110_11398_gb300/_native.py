@@ -23,7 +23,7 @@ EXPORTS = ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_
            "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
            "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
            "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift", "nf_timestep",
-           "nf_kdk_step",
+           "nf_kdk_step", "nf_far_init", "nf_compute_far",
            "nf_last_error", "nf_status_string", "nf_free")
 
 
@@ -81,6 +81,8 @@ def load(path: str | None = None):
         lib.nf_drift.argtypes = [vp, vp, vp, dbl, vp]
         lib.nf_timestep.argtypes = [vp, vp, vp, dbl, P(dbl), vp]
         lib.nf_kdk_step.argtypes = [vp, vp, vp, vp, vp, dbl, dbl, P(i64), vp]
+        lib.nf_far_init.argtypes = [vp, i32, vp]
+        lib.nf_compute_far.argtypes = [vp, vp, i32, vp]
         lib.nf_accel_host.argtypes = [vp, vp, vp, dbl, i64, P(i64), vp, vp]
         lib.nf_get_stats.argtypes = [vp, P(nf_stats)]
         lib.nf_set_tuning.argtypes = [vp, P(nf_tuning)]
@@ -97,7 +99,7 @@ def load(path: str | None = None):
         for name in ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
                      "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
                      "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
-                     "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift",
+                     "nf_far_init", "nf_compute_far", "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift",
                      "nf_timestep", "nf_kdk_step"):
             getattr(lib, name).restype = i32
         _lib = lib

@@ -71,6 +71,7 @@ void release(Ctx *c) {
     if (c->g_fwd.exec) cudaGraphExecDestroy(c->g_fwd.exec);
     if (c->g_vjp.exec) cudaGraphExecDestroy(c->g_vjp.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    far_release(c);
     cudaEvent_t evs[] = {c->ev_bin0, c->ev_bin1, c->ev_pair0, c->ev_pair1};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
@@ -515,6 +516,35 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
     }
     if (e) return cuda_fail(c, e, "nf_compute_accel_vjp");
     c->have_pair_time = 1;
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_far_init(nf_ctx *ctx, int order, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_far_init: ctx is NULL");
+    if (c->n_boxes != 1) return fail(c, NF_EINVAL, "nf_far_init: the far field needs a one-box context");
+    if (order < 1 || order > 8) return fail(c, NF_EINVAL, "nf_far_init: order must be in [1, 8]");
+    if (c->boxes_h[0].cpd > 192) return fail(c, NF_EINVAL, "nf_far_init: CPD above 192 is not supported");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    std::string err;
+    const int rc = far_setup(c, order, s, err);
+    if (rc) return fail(c, rc, err);
+    return NF_OK;
+}
+
+int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_compute_far: ctx is NULL");
+    if (!c->far) return fail(c, NF_ESTATE, "nf_compute_far: call nf_far_init first");
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_far: no binned particles");
+    if (c->n > 0 && !acc) return fail(c, NF_EINVAL, "nf_compute_far: acc is required");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (c->n == 0) return NF_OK;
+    cudaError_t e = far_compute(c, acc, accumulate ? 1 : 0, s);
+    if (e) return cuda_fail(c, e, "nf_compute_far");
     c->last_stream = s;
     return NF_OK;
 }

@@ -11,6 +11,8 @@
 
 namespace nf {
 
+struct FarState;   // far-field state (nf_far.cu)
+
 // A captured phase of work replayed as a CUDA graph; `key` holds the
 // arguments baked into the capture.
 struct GraphSlot {
@@ -85,8 +87,15 @@ struct Ctx {
     int64_t launches = 0;
     int have_bin_time = 0, have_pair_time = 0;
 
+    FarState *far = nullptr;                       // far field (nf_far_init), one-box contexts
+
     std::string err;
 };
+
+// far field (nf_far.cu)
+int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err);
+cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s);
+void far_release(Ctx *c);
 
 constexpr int kMomBlocks = 512;
 

@@ -1,0 +1,586 @@
+// nf_far.cu -- far field of the near/far split (Maksimova et al. 2021,
+// Sec. 3.1): Taylor series of order p about every cell centre, whose
+// coefficients are the cyclic convolution, over the CPD^3 cells and carried
+// out in Fourier space, of the cells' multipole moments with the derivatives
+// tensor of the periodic Green's function; the tensor depends on the grid
+// only and is built once per context.
+//
+// Conventions (cell units, origin at the cell centre):
+//   multipoles    M_m(c)  = sum_{j in c} G m_j z_j^m,          |m| <= p
+//   tensor        D_q(d)  = sum over periodic images of d^q (1/r) at d + n CPD,
+//                           the image inside the near field ([-R, R]^3) left
+//                           out; Ewald sum with a uniform background, |q| <= 2p
+//   Taylor        T_k(c)  = sum_c' sum_m (-1)^|m| / m!  D_{k+m}(c - c') M_m(c')
+//   acceleration  a(y)    = grad_y sum_k T_k y^k / k!   (times (CPD / L)^2)
+// The tensor is split as in Ewald's method: d^q [erfc(alpha r)/r] summed in
+// real space over the few lattice vectors it reaches (on the host, once), and
+// the rest, (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q, written straight into
+// its discrete Fourier transform. cuFFT does the transforms; the multipoles,
+// the per-frequency products and the Taylor gradient are kernels here.
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "nf_ctx.h"
+#include "nf_internal.cuh"
+
+namespace nf {
+
+// Multi-indices (a, b, c), a + b + c <= n, enumerated by degree, then c
+// ascending, then b ascending (a = degree - b - c).
+struct MultiIndex {
+    int n = 0;
+    std::vector<int> a, b, c;
+    std::vector<int> pos;   // (a, b, c) -> position, (n+1)^3 table, -1 where a+b+c > n
+    void build(int order) {
+        n = order;
+        a.clear(); b.clear(); c.clear();
+        pos.assign((size_t)(n + 1) * (n + 1) * (n + 1), -1);
+        for (int t = 0; t <= n; ++t)
+            for (int cc = 0; cc <= t; ++cc)
+                for (int bb = 0; bb <= t - cc; ++bb) {
+                    const int aa = t - bb - cc;
+                    pos[((size_t)aa * (n + 1) + bb) * (n + 1) + cc] = (int)a.size();
+                    a.push_back(aa); b.push_back(bb); c.push_back(cc);
+                }
+    }
+    int size() const { return (int)a.size(); }
+    int at(int aa, int bb, int cc) const { return pos[((size_t)aa * (n + 1) + bb) * (n + 1) + cc]; }
+};
+
+struct FarState {
+    int p = 0, P = 0, np = 0, nq = 0;
+    double alpha = 0.0;
+    int64_t ncell = 0, nfreq = 0;
+    double *M = nullptr;             // [np][ncell] multipoles, then reused for T
+    cufftDoubleComplex *Mh = nullptr;  // [np][nfreq]
+    cufftDoubleComplex *Th = nullptr;  // [np][nfreq]
+    cufftDoubleComplex *Dh = nullptr;  // [nq][nfreq]
+    int *mabc = nullptr;             // [3][np] multi-indices of order <= p (device)
+    int *conv_add = nullptr;         // [np][np]: position of k + m among the order-2p indices
+    double *conv_coef = nullptr;     // [np]: (-1)^|m| / m!
+    int *tay = nullptr;              // [4][ntay]: Taylor-gradient table (see k_far_taylor)
+    int ntay = 0;
+    cufftHandle r2c = 0, c2r = 0;
+    bool r2c_ok = false, c2r_ok = false;
+};
+
+namespace {
+
+// ------------------------------------------------------------ host: short-range tensor
+// (1/r d/dr)^n of the two radial functions of the real-space part.
+// erfc(alpha r)/r: h_n = (-1)^n B_n, B_0 = erfc(alpha r)/r,
+//   B_n = ((2n - 1) B_{n-1} + (2 alpha^2)^n exp(-alpha^2 r^2) / (alpha sqrt(pi))) / r^2.
+void radial_erfc(double r, double alpha, int n_max, double *h) {
+    const double gauss = std::exp(-alpha * alpha * r * r) / (alpha * std::sqrt(M_PI));
+    double B = std::erfc(alpha * r) / r, pw = 1.0;
+    h[0] = B;
+    for (int n = 1; n <= n_max; ++n) {
+        pw *= 2.0 * alpha * alpha;
+        B = ((2 * n - 1) * B + pw * gauss) / (r * r);
+        h[n] = (n & 1) ? -B : B;
+    }
+}
+
+// -erf(alpha r)/r (the near image: erfc/r minus the 1/r that the near field
+// already has), from its power series, which has no cancellation at r ~ 1/alpha:
+//   h_n = -(2 alpha / sqrt(pi)) (-2 alpha^2)^n sum_j (-alpha^2 r^2)^j / (j! (2n + 2j + 1)).
+void radial_minus_erf(double r, double alpha, int n_max, double *h) {
+    const double x = alpha * alpha * r * r;
+    double lead = -2.0 * alpha / std::sqrt(M_PI);
+    for (int n = 0; n <= n_max; ++n) {
+        double t = 1.0, s = 0.0;
+        for (int j = 0; j < 400; ++j) {
+            const double term = t / (2.0 * (n + j) + 1.0);
+            s += term;
+            if (j > x && std::fabs(term) < 1e-19 * std::fabs(s)) break;
+            t *= -x / (j + 1);
+        }
+        h[n] = lead * s;
+        lead *= -2.0 * alpha * alpha;
+    }
+}
+
+// All Cartesian derivatives d^(a,b,c) f at v, |(a,b,c)| <= mi.n, of a radial
+// function given h_n = (1/r d/dr)^n f: the Hermite-type recursion
+//   H^(n)_{a,b,c} = v_x H^(n+1)_{a-1,b,c} + (a - 1) H^(n+1)_{a-2,b,c}
+// (likewise along y and z), H^(n)_000 = h_n, d^(a,b,c) f = H^(0)_abc.
+void cartesian_derivs(const double v[3], const double *h, const MultiIndex &mi,
+                      std::vector<double> &H, double *out) {
+    const int n = mi.n, N = mi.size();
+    H.resize((size_t)(n + 1) * N);
+    for (int i = 0; i < N; ++i) {
+        const int a = mi.a[i], b = mi.b[i], c = mi.c[i], deg = a + b + c;
+        for (int l = 0; l + deg <= n; ++l) {
+            double val;
+            if (deg == 0) {
+                val = h[l];
+            } else if (c > 0) {
+                val = v[2] * H[(size_t)(l + 1) * N + mi.at(a, b, c - 1)];
+                if (c > 1) val += (c - 1) * H[(size_t)(l + 1) * N + mi.at(a, b, c - 2)];
+            } else if (b > 0) {
+                val = v[1] * H[(size_t)(l + 1) * N + mi.at(a, b - 1, c)];
+                if (b > 1) val += (b - 1) * H[(size_t)(l + 1) * N + mi.at(a, b - 2, c)];
+            } else {
+                val = v[0] * H[(size_t)(l + 1) * N + mi.at(a - 1, b, c)];
+                if (a > 1) val += (a - 1) * H[(size_t)(l + 1) * N + mi.at(a - 2, b, c)];
+            }
+            H[(size_t)l * N + i] = val;
+        }
+    }
+    for (int i = 0; i < N; ++i) out[i] += H[i];
+}
+
+// Real-space part of the tensor: every integer lattice vector s with
+// |s| < r_cut contributes d^q[erfc(alpha r)/r](s) to grid cell s mod P; the
+// near-field vectors (s in [-R, R]^3) contribute d^q[-erf(alpha r)/r](s).
+// Returns the touched cells and their nq values. Vectors are grouped by cell
+// and each cell is summed by one thread in a fixed order, so the result does
+// not depend on the thread count.
+void real_space_part(int P, int R, double alpha, double r_cut, const MultiIndex &mq,
+                     std::vector<int64_t> &cells, std::vector<double> &vals) {
+    const int nq = mq.size();
+    const int smax = (int)std::ceil(r_cut);
+    struct Vec { int64_t cell; int x, y, z; };
+    std::vector<Vec> vecs;
+    for (int x = -smax; x <= smax; ++x)
+        for (int y = -smax; y <= smax; ++y)
+            for (int z = -smax; z <= smax; ++z) {
+                const bool near = std::abs(x) <= R && std::abs(y) <= R && std::abs(z) <= R;
+                if (!near && std::sqrt((double)x * x + (double)y * y + (double)z * z) >= r_cut) continue;
+                const int64_t g = ((int64_t)(((x % P) + P) % P) * P + ((y % P) + P) % P) * P + ((z % P) + P) % P;
+                vecs.push_back({g, x, y, z});
+            }
+    std::stable_sort(vecs.begin(), vecs.end(), [](const Vec &u, const Vec &v) { return u.cell < v.cell; });
+    std::vector<size_t> first;   // start of each cell's run in vecs
+    cells.clear();
+    for (size_t i = 0; i < vecs.size(); ++i)
+        if (i == 0 || vecs[i].cell != vecs[i - 1].cell) { first.push_back(i); cells.push_back(vecs[i].cell); }
+    first.push_back(vecs.size());
+    vals.assign(cells.size() * (size_t)nq, 0.0);
+    const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            std::vector<double> H;
+            double h[64];
+            for (size_t g = t; g < cells.size(); g += nt)
+                for (size_t i = first[g]; i < first[g + 1]; ++i) {
+                    const Vec &v = vecs[i];
+                    const double sv[3] = {(double)v.x, (double)v.y, (double)v.z};
+                    const double r = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
+                    const bool near = std::abs(v.x) <= R && std::abs(v.y) <= R && std::abs(v.z) <= R;
+                    if (near) radial_minus_erf(r, alpha, mq.n, h);
+                    else radial_erfc(r, alpha, mq.n, h);
+                    cartesian_derivs(sv, h, mq, H, vals.data() + g * (size_t)nq);
+                }
+        });
+    for (auto &x : th) x.join();
+}
+
+// ------------------------------------------------------------ kernels
+__global__ void k_far_scatter(const double *__restrict__ vals, const int64_t *__restrict__ cells,
+                              int64_t n_cells_touched, int nq, int64_t ncell, double *__restrict__ grid) {
+    const int64_t total = n_cells_touched * nq;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / nq;
+        const int q = (int)(i - t * nq);
+        grid[(int64_t)q * ncell + cells[t]] = vals[i];
+    }
+}
+
+// Long-range part, added in Fourier space: for frequency w (cuFFT R2C layout
+// [x][y][z <= P/2]) and every alias m = w + G P with 0 < |k| < k_cut,
+// k = 2 pi m / P:  Dh_q(w) += (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q.
+__global__ void k_far_longrange(cufftDoubleComplex *__restrict__ Dh, int P, int64_t nfreq, int nq,
+                                const int *__restrict__ qa, const int *__restrict__ qb,
+                                const int *__restrict__ qc, double alpha, double k_cut) {
+    const int Pz = P / 2 + 1;
+    const double two_pi_P = 2.0 * M_PI / P;
+    const int G = (int)ceil(k_cut / (2.0 * M_PI)) + 1;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfreq;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        const int wz = (int)(f % Pz), wy = (int)((f / Pz) % P), wx = (int)(f / ((int64_t)Pz * P));
+        for (int gx = -G; gx <= G; ++gx)
+            for (int gy = -G; gy <= G; ++gy)
+                for (int gz = -G; gz <= G; ++gz) {
+                    const int mx = wx + gx * P, my = wy + gy * P, mz = wz + gz * P;
+                    if (mx == 0 && my == 0 && mz == 0) continue;
+                    const double kx = two_pi_P * mx, ky = two_pi_P * my, kz = two_pi_P * mz;
+                    const double k2 = kx * kx + ky * ky + kz * kz;
+                    if (k2 >= k_cut * k_cut) continue;
+                    const double w = 4.0 * M_PI / k2 * exp(-k2 / (4.0 * alpha * alpha));
+                    double px[33], py[33], pz[33];
+                    px[0] = py[0] = pz[0] = 1.0;
+                    for (int j = 1; j < 33; ++j) {
+                        px[j] = px[j - 1] * kx; py[j] = py[j - 1] * ky; pz[j] = pz[j - 1] * kz;
+                    }
+                    for (int q = 0; q < nq; ++q) {
+                        const int a = qa[q], b = qb[q], c = qc[q];
+                        const double v = w * px[a] * py[b] * pz[c];
+                        cufftDoubleComplex &d = Dh[(int64_t)q * nfreq + f];
+                        switch ((a + b + c) & 3) {   // i^|q|
+                            case 0: d.x += v; break;
+                            case 1: d.y += v; break;
+                            case 2: d.x -= v; break;
+                            default: d.y -= v; break;
+                        }
+                    }
+                }
+    }
+}
+
+// Multipoles: one block per cell, 128 threads. A tile of up to 128 sorted
+// records is staged with each particle's powers x^e, y^e, z^e (e <= p,
+// particle-major so that a warp reading one particle's powers hits distinct
+// banks or one broadcast); thread t then owns components t and t + 128 and
+// sums mass * x^a y^b z^c over the tile in FP32, folded into an FP64 total
+// per tile.
+constexpr int kFarThreads = 128;
+constexpr int kFarMaxP = 8;
+
+__global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
+    const float4 *__restrict__ sorted, const int *__restrict__ cell_start, int64_t ncell, int p, int np,
+    const int *__restrict__ mabc, double *__restrict__ M) {
+    __shared__ float pw[3][kFarThreads][kFarMaxP + 1];
+    __shared__ float ms[kFarThreads];
+    const int t = threadIdx.x;
+    const int i0 = t, i1 = t + kFarThreads;
+    int a0 = 0, b0 = 0, c0 = 0, a1 = 0, b1 = 0, c1 = 0;
+    if (i0 < np) { a0 = mabc[i0]; b0 = mabc[np + i0]; c0 = mabc[2 * np + i0]; }
+    if (i1 < np) { a1 = mabc[i1]; b1 = mabc[np + i1]; c1 = mabc[2 * np + i1]; }
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+        const int s = cell_start[cell], e = cell_start[cell + 1];
+        double acc0 = 0.0, acc1 = 0.0;
+        for (int base = s; base < e; base += kFarThreads) {
+            const int cnt = min(kFarThreads, e - base);
+            __syncthreads();
+            if (t < cnt) {
+                const float4 r = sorted[base + t];
+                pw[0][t][0] = pw[1][t][0] = pw[2][t][0] = 1.f;
+                for (int j = 1; j <= p; ++j) {
+                    pw[0][t][j] = pw[0][t][j - 1] * r.x;
+                    pw[1][t][j] = pw[1][t][j - 1] * r.y;
+                    pw[2][t][j] = pw[2][t][j - 1] * r.z;
+                }
+                ms[t] = r.w;
+            }
+            __syncthreads();
+            float f0 = 0.f, f1 = 0.f;
+            for (int j = 0; j < cnt; ++j) {
+                const float m = ms[j];
+                f0 = fmaf(m * pw[0][j][a0] * pw[1][j][b0], pw[2][j][c0], f0);
+                f1 = fmaf(m * pw[0][j][a1] * pw[1][j][b1], pw[2][j][c1], f1);
+            }
+            acc0 += (double)f0;
+            acc1 += (double)f1;
+        }
+        if (i0 < np) M[(int64_t)i0 * ncell + cell] = acc0;
+        if (i1 < np) M[(int64_t)i1 * ncell + cell] = acc1;
+    }
+}
+
+// Per-frequency products T_k(w) = sum_m coef_m D_{k+m}(w) M_m(w): a block
+// takes 32 consecutive frequencies (one per lane); coef_m M_m(w) is staged in
+// shared memory; warp y of the block computes k = y, y + blockDim.y, ...
+__global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
+                               const cufftDoubleComplex *__restrict__ Mh,
+                               cufftDoubleComplex *__restrict__ Th, int64_t nfreq, int np,
+                               const int *__restrict__ add, const double *__restrict__ coef) {
+    extern __shared__ double2 cm[];   // [np][32]
+    const int lane = threadIdx.x, wy = threadIdx.y, ny = blockDim.y;
+    for (int64_t f0 = (int64_t)blockIdx.x * 32; f0 < nfreq; f0 += (int64_t)gridDim.x * 32) {
+        const int64_t f = f0 + lane;
+        const bool ok = f < nfreq;
+        __syncthreads();
+        for (int m = wy; m < np; m += ny) {
+            double2 v = make_double2(0.0, 0.0);
+            if (ok) {
+                const cufftDoubleComplex x = Mh[(int64_t)m * nfreq + f];
+                const double cf = coef[m];
+                v = make_double2(cf * x.x, cf * x.y);
+            }
+            cm[m * 32 + lane] = v;
+        }
+        __syncthreads();
+        for (int k = wy; k < np; k += ny) {
+            double re = 0.0, im = 0.0;
+            const int *ak = add + (int64_t)k * np;
+            if (ok) {
+                for (int m = 0; m < np; ++m) {
+                    const cufftDoubleComplex d = Dh[(int64_t)__ldg(&ak[m]) * nfreq + f];
+                    const double2 x = cm[m * 32 + lane];
+                    re = fma(d.x, x.x, fma(-d.y, x.y, re));
+                    im = fma(d.x, x.y, fma(d.y, x.x, im));
+                }
+                Th[(int64_t)k * nfreq + f] = make_double2(re, im);
+            }
+        }
+    }
+}
+
+// Taylor gradient at every particle: one block per cell; the cell's T_k
+// (scaled to box units) are staged in shared memory as floats; each thread
+// takes a particle y and sums, over |j| <= p - 1,
+//   (y^j / j!) (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}).
+// tay[0..3][i] = (a, b, c) of j and, packed, the positions of j + e_x,
+// j + e_y, j + e_z among the order-p indices (10 bits each).
+__global__ void __launch_bounds__(kFarThreads) k_far_taylor(
+    const float4 *__restrict__ sorted, const int *__restrict__ cell_start, const int *__restrict__ perm,
+    const double *__restrict__ T, int64_t ncell, int p, int np, const int *__restrict__ tay, int ntay,
+    double scale, float *__restrict__ acc, int accumulate) {
+    __shared__ float Ts[kFarThreads * 2];
+    __shared__ int tj[4][kFarThreads];
+    const int t = threadIdx.x;
+    for (int i = t; i < ntay; i += kFarThreads)
+        for (int r = 0; r < 4; ++r) tj[r][i] = tay[r * ntay + i];
+    float inv_fact[kFarMaxP + 1];
+    inv_fact[0] = 1.f;
+    for (int j = 1; j <= kFarMaxP; ++j) inv_fact[j] = inv_fact[j - 1] / (float)j;
+    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
+        const int s = cell_start[cell], e = cell_start[cell + 1];
+        if (s == e) continue;   // uniform over the block
+        __syncthreads();
+        for (int i = t; i < np; i += kFarThreads) Ts[i] = (float)(T[(int64_t)i * ncell + cell] * scale);
+        __syncthreads();
+        for (int j = s + t; j < e; j += kFarThreads) {
+            const float4 r = sorted[j];
+            float px[kFarMaxP], py[kFarMaxP], pz[kFarMaxP];   // y^e / e!
+            px[0] = py[0] = pz[0] = 1.f;
+            for (int q = 1; q < p; ++q) {
+                px[q] = px[q - 1] * r.x;
+                py[q] = py[q - 1] * r.y;
+                pz[q] = pz[q - 1] * r.z;
+            }
+            for (int q = 1; q < p; ++q) {
+                px[q] *= inv_fact[q];
+                py[q] *= inv_fact[q];
+                pz[q] *= inv_fact[q];
+            }
+            float ax = 0.f, ay = 0.f, az = 0.f;
+            for (int i = 0; i < ntay; ++i) {
+                const float y = px[tj[0][i]] * py[tj[1][i]] * pz[tj[2][i]];
+                const int pk = tj[3][i];
+                ax = fmaf(y, Ts[pk & 1023], ax);
+                ay = fmaf(y, Ts[(pk >> 10) & 1023], ay);
+                az = fmaf(y, Ts[pk >> 20], az);
+            }
+            float *o = acc + 3 * (int64_t)perm[j];
+            if (accumulate) {
+                o[0] += ax; o[1] += ay; o[2] += az;
+            } else {
+                o[0] = ax; o[1] = ay; o[2] = az;
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t dmalloc(T **p, size_t count) {
+    *p = nullptr;
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * (count ? count : 1));
+}
+
+template <typename T>
+cudaError_t upload(T **d, const std::vector<T> &h) {
+    cudaError_t e = dmalloc(d, h.size());
+    if (e) return e;
+    return cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+int grid_blocks(int64_t n, int threads, int sm_count, int per_sm) {
+    int64_t g = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)sm_count * per_sm;
+    return (int)std::max<int64_t>(1, std::min(g, cap));
+}
+
+}  // namespace
+
+void far_release(Ctx *c) {
+    FarState *f = c->far;
+    if (!f) return;
+    void *bufs[] = {f->M, f->Mh, f->Th, f->Dh, f->mabc, f->conv_add, f->conv_coef, f->tay};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (f->r2c_ok) cufftDestroy(f->r2c);
+    if (f->c2r_ok) cufftDestroy(f->c2r);
+    delete f;
+    c->far = nullptr;
+}
+
+// Builds the far-field state of a one-box context: index tables, the
+// derivatives tensor in Fourier space, buffers and FFT plans. Synchronous.
+// Returns NF_OK, or NF_ENOMEM / NF_ECUDA with `err` set.
+int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
+    far_release(c);
+    FarState *f = new FarState();
+    c->far = f;
+    const BoxDev &B = c->boxes_h[0];
+    f->p = order;
+    f->P = B.cpd;
+    const int P = f->P;
+    f->ncell = (int64_t)P * P * P;
+    f->nfreq = (int64_t)P * P * (P / 2 + 1);
+    MultiIndex mp, mq;
+    mp.build(order);
+    mq.build(2 * order);
+    f->np = mp.size();
+    f->nq = mq.size();
+    // splitting: the real-space part reaches r < (6.5 + q/4)/alpha cells and the
+    // Fourier part |k| < (13 + q/2) alpha; alpha = max(0.5, 3.5/P) keeps both small
+    f->alpha = std::max(0.5, 3.5 / P);
+    const double r_cut = (6.5 + 0.25 * mq.n) / f->alpha;
+    const double k_cut = (13.0 + 0.5 * mq.n) * f->alpha;
+    auto cuda_err = [&](cudaError_t e, const char *what) {
+        err = std::string("nf_far_init: ") + what + ": " + cudaGetErrorString(e);
+        far_release(c);
+        return e == cudaErrorMemoryAllocation ? NF_ENOMEM : NF_ECUDA;
+    };
+    auto fft_err = [&](cufftResult r, const char *what) {
+        err = std::string("nf_far_init: ") + what + ": cuFFT error " + std::to_string((int)r);
+        far_release(c);
+        return r == CUFFT_ALLOC_FAILED ? NF_ENOMEM : NF_ECUDA;
+    };
+    cudaError_t e;
+    // index tables
+    {
+        std::vector<int> mabc(3 * (size_t)f->np), add((size_t)f->np * f->np), qabc(3 * (size_t)f->nq);
+        std::vector<double> coef(f->np);
+        for (int i = 0; i < f->np; ++i) {
+            mabc[i] = mp.a[i]; mabc[f->np + i] = mp.b[i]; mabc[2 * f->np + i] = mp.c[i];
+            double fac = 1.0;
+            for (int x = 2; x <= mp.a[i]; ++x) fac *= x;
+            for (int x = 2; x <= mp.b[i]; ++x) fac *= x;
+            for (int x = 2; x <= mp.c[i]; ++x) fac *= x;
+            coef[i] = (((mp.a[i] + mp.b[i] + mp.c[i]) & 1) ? -1.0 : 1.0) / fac;
+        }
+        for (int k = 0; k < f->np; ++k)
+            for (int m = 0; m < f->np; ++m)
+                add[(size_t)k * f->np + m] = mq.at(mp.a[k] + mp.a[m], mp.b[k] + mp.b[m], mp.c[k] + mp.c[m]);
+        for (int i = 0; i < f->nq; ++i) {
+            qabc[i] = mq.a[i]; qabc[f->nq + i] = mq.b[i]; qabc[2 * f->nq + i] = mq.c[i];
+        }
+        // Taylor gradient: every j with |j| <= p - 1
+        std::vector<int> ja, jb, jc, jp;
+        for (int i = 0; i < f->np; ++i) {
+            if (mp.a[i] + mp.b[i] + mp.c[i] > order - 1) continue;
+            ja.push_back(mp.a[i]); jb.push_back(mp.b[i]); jc.push_back(mp.c[i]);
+            jp.push_back(mp.at(mp.a[i] + 1, mp.b[i], mp.c[i]) | (mp.at(mp.a[i], mp.b[i] + 1, mp.c[i]) << 10) |
+                         (mp.at(mp.a[i], mp.b[i], mp.c[i] + 1) << 20));
+        }
+        f->ntay = (int)ja.size();
+        std::vector<int> tay;
+        tay.insert(tay.end(), ja.begin(), ja.end());
+        tay.insert(tay.end(), jb.begin(), jb.end());
+        tay.insert(tay.end(), jc.begin(), jc.end());
+        tay.insert(tay.end(), jp.begin(), jp.end());
+        if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->conv_add, add)) ||
+            (e = upload(&f->conv_coef, coef)) || (e = upload(&f->tay, tay)))
+            return cuda_err(e, "tables");
+        int *qa = nullptr;
+        if ((e = upload(&qa, qabc))) return cuda_err(e, "tables");
+        // real-space part (host), scattered into a zeroed FP64 grid
+        std::vector<int64_t> cells;
+        std::vector<double> vals;
+        real_space_part(P, c->R, f->alpha, r_cut, mq, cells, vals);
+        double *grid = nullptr, *dvals = nullptr;
+        int64_t *dcells = nullptr;
+        if ((e = dmalloc(&f->Dh, (size_t)f->nq * f->nfreq))) { cudaFree(qa); return cuda_err(e, "tensor"); }
+        if ((e = dmalloc(&grid, (size_t)f->nq * f->ncell)) || (e = upload(&dvals, vals)) || (e = upload(&dcells, cells))) {
+            cudaFree(qa); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+            return cuda_err(e, "tensor");
+        }
+        e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nq * f->ncell, s);
+        if (!e) {
+            k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nq, 256, c->sm_count, 8), 256, 0, s>>>(
+                dvals, dcells, (int64_t)cells.size(), f->nq, f->ncell, grid);
+            e = cudaGetLastError();
+        }
+        // forward transforms of the tensor, a few components per plan execution
+        // the tensor's components are transformed 64 at a time, the rest by a
+        // second plan: chunk starts stay at even component offsets, which
+        // keeps them 16-byte aligned as cuFFT requires of its data
+        cufftHandle plan = 0, plan_rest = 0;
+        int dims[3] = {P, P, P};
+        const int chunk = 64, rest = f->nq % chunk;
+        const char *stage = "tensor transform: plan";
+        cufftResult fr = CUFFT_SUCCESS;
+        if (!e && f->nq >= chunk)
+            fr = cufftPlanMany(&plan, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, chunk);
+        if (!e && fr == CUFFT_SUCCESS && rest)
+            fr = cufftPlanMany(&plan_rest, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, rest);
+        if (!e && fr == CUFFT_SUCCESS) {
+            stage = "tensor transform: stream";
+            if (plan) fr = cufftSetStream(plan, s);
+            if (fr == CUFFT_SUCCESS && plan_rest) fr = cufftSetStream(plan_rest, s);
+        }
+        for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nq; q0 += chunk) {
+            stage = "tensor transform: exec";
+            fr = cufftExecD2Z(q0 + chunk <= f->nq ? plan : plan_rest, grid + (size_t)q0 * f->ncell,
+                              f->Dh + (size_t)q0 * f->nfreq);
+        }
+        if (!e && fr == CUFFT_SUCCESS) {
+            k_far_longrange<<<grid_blocks(f->nfreq, 128, c->sm_count, 8), 128, 0, s>>>(
+                f->Dh, P, f->nfreq, f->nq, qa, qa + f->nq, qa + 2 * f->nq, f->alpha, k_cut);
+            e = cudaGetLastError();
+        }
+        if (!e) e = cudaStreamSynchronize(s);
+        if (plan) cufftDestroy(plan);
+        if (plan_rest) cufftDestroy(plan_rest);
+        cudaFree(qa); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+        if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
+        if (e) return cuda_err(e, "tensor");
+    }
+    // per-step buffers and plans
+    if ((e = dmalloc(&f->M, (size_t)f->np * f->ncell)) || (e = dmalloc(&f->Mh, (size_t)f->np * f->nfreq)) ||
+        (e = dmalloc(&f->Th, (size_t)f->np * f->nfreq)))
+        return cuda_err(e, "buffers");
+    int dims[3] = {P, P, P};
+    cufftResult fr = cufftPlanMany(&f->r2c, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq,
+                                   CUFFT_D2Z, f->np);
+    if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
+    f->r2c_ok = true;
+    fr = cufftPlanMany(&f->c2r, 3, dims, nullptr, 1, (int)f->nfreq, nullptr, 1, (int)f->ncell, CUFFT_Z2D, f->np);
+    if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
+    f->c2r_ok = true;
+    return NF_OK;
+}
+
+// Far-field accelerations of the binned particles, input order, written to
+// (or, with accumulate, added into) acc. Enqueued on s.
+cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
+    FarState *f = c->far;
+    const BoxDev &B = c->boxes_h[0];
+    k_far_multipoles<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->M);
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if (cufftSetStream(f->r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(f->r2c, f->M, f->Mh) != CUFFT_SUCCESS)
+        return cudaErrorUnknown;
+    const int ny = 8;
+    const size_t smem = sizeof(double2) * 32 * (size_t)f->np;
+    e = cudaFuncSetAttribute(k_far_convolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return e;
+    k_far_convolve<<<grid_blocks(f->nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
+        f->Dh, f->Mh, f->Th, f->nfreq, f->np, f->conv_add, f->conv_coef);
+    c->launches += 1;
+    if ((e = cudaGetLastError())) return e;
+    if (cufftSetStream(f->c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(f->c2r, f->Th, f->M) != CUFFT_SUCCESS)
+        return cudaErrorUnknown;
+    // T = inverse transform / P^3; acceleration in box units = cell units * inv_h2
+    const double scale = B.inv_h2_d / (double)f->ncell;
+    k_far_taylor<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+        c->sorted, c->cell_start, c->perm, f->M, f->ncell, f->p, f->np, f->tay, f->ntay, scale, acc, accumulate);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace nf

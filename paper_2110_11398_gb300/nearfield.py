@@ -186,6 +186,25 @@ class NearField:
         N.check(rc, self._ctx, "nf_compute_accel_vjp")
         return out
 
+    # ------------------------------------------------------------ far field
+    def far_init(self, order: int = 8) -> None:
+        """Enable the far field of order ``order`` (one-box contexts): builds
+        the derivatives tensor for this CPD and near-field radius."""
+        N.check(self._lib.nf_far_init(self._ctx, int(order), _stream_ptr(self.device)), self._ctx,
+                "nf_far_init")
+
+    def far(self, out: torch.Tensor | None = None, accumulate: bool = False) -> torch.Tensor:
+        """Far-field accelerations of the binned particles (input order); with
+        ``accumulate`` they are added into ``out`` (e.g. the near field)."""
+        if out is None:
+            if accumulate:
+                raise ValueError("accumulate needs an out tensor")
+            out = torch.empty((self.n, 3), dtype=torch.float32, device=self.device)
+        out = self._check_vec3(out, "out")
+        N.check(self._lib.nf_compute_far(self._ctx, out.data_ptr() if self.n else None, int(bool(accumulate)),
+                                         _stream_ptr(self.device)), self._ctx, "nf_compute_far")
+        return out
+
     # ------------------------------------------------------------ particle update
     def kick(self, vel: torch.Tensor, acc: torch.Tensor, dt: float) -> None:
         """v += a dt (in place)."""

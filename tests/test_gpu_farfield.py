@@ -1,0 +1,124 @@
+"""GPU far field (multipoles, derivatives tensor, Taylor series of order p;
+Maksimova et al. 2021, Sec. 3.1) against the FP64 oracle of the same method,
+and near + far against the Ewald sum of the periodic 1/r^2 force.
+
+The GPU forms the multipoles from the FP32 cell-relative records and
+evaluates the Taylor series in FP32 (the tensor and the convolution are
+FP64), so it agrees with the FP64 oracle of the same method to about the
+FP32 rounding of the far field; the method itself is within 1e-5 of the
+Ewald force at p = 8.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2110_11398_gb300 import build
+    build.build()
+    return torch.device("cuda", 0)
+
+
+def rel(got, ref):
+    return np.linalg.norm(np.asarray(got, np.float64) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+def far_gpu(pos, L, cpd, eps, dev, p=8, mass=None, gm=None, R=2):
+    from paper_2110_11398_gb300 import NearField
+    nf = NearField(L, cpd, eps, radius=R, capacity=len(pos), device=dev)
+    nf.far_init(p)
+    m = None if mass is None else torch.from_numpy(mass.astype(np.float32)).to(dev)
+    nf.bin(torch.from_numpy(pos.astype(np.float32)).to(dev), m, gm=gm)
+    far = nf.far().cpu().numpy()
+    near = nf.accel().cpu().numpy()
+    nf.close()
+    return far, near
+
+
+@pytest.mark.parametrize("p", [4, 8])
+def test_far_matches_the_oracle(dev, p):
+    rng = np.random.default_rng(1)
+    n, L, cpd = 3000, 1.0, 7
+    pos = rng.random((n, 3)).astype(np.float32)
+    mass = (rng.uniform(0.5, 1.5, n) / n).astype(np.float32)
+    got, _ = far_gpu(pos, L, cpd, 1e-3, dev, p=p, mass=mass)
+    ref = oracle.far_accel(pos.astype(np.float64), L, cpd, 2, p, mass=mass.astype(np.float64))
+    e = rel(got, ref)
+    assert np.median(e) < 2e-6 and np.quantile(e, 0.999) < 1e-4, (np.median(e), np.quantile(e, 0.999))
+
+
+def test_far_equal_masses_clustered_box(dev):
+    pos, _ = synth.clustered_box(24 ** 3, 3, n_halos=8)
+    L, cpd = 1.0, 8
+    gm = 1.0 / len(pos)
+    got, _ = far_gpu(pos, L, cpd, 1e-4, dev, p=8, gm=gm)
+    idx = np.arange(0, len(pos), 5)
+    ref = oracle.far_accel(pos.astype(np.float64), L, cpd, 2, 8, m0=gm)[idx]
+    e = rel(got[idx], ref)
+    assert np.median(e) < 2e-6 and np.quantile(e, 0.999) < 1e-4, (np.median(e), np.quantile(e, 0.999))
+
+
+def test_near_plus_far_is_the_ewald_force(dev):
+    """With (almost) no softening, near field + far field at p = 8 is the
+    total periodic force."""
+    rng = np.random.default_rng(2)
+    n, L, cpd = 600, 1.0, 7
+    pos = rng.random((n, 3)).astype(np.float32)
+    mass = (rng.uniform(0.5, 1.5, n) / n).astype(np.float32)
+    far, near = far_gpu(pos, L, cpd, 1e-7, dev, p=8, mass=mass)
+    tot = oracle.ewald_accel(pos.astype(np.float64), L, mass=mass.astype(np.float64))
+    e = rel(far.astype(np.float64) + near, tot)
+    assert np.median(e) < 2e-6 and e.max() < 1e-3, (np.median(e), e.max())
+
+
+def test_far_accumulates_onto_the_near_field(dev):
+    from paper_2110_11398_gb300 import NearField
+    box = synth.tiny()
+    nf = NearField(box.L, box.cpd, box.eps, capacity=box.n, device=dev)
+    nf.far_init(6)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    near = nf.accel()
+    far = nf.far()
+    both = nf.far(out=near.clone(), accumulate=True)
+    assert torch.equal(both, near + far)
+    nf.close()
+
+
+def test_far_is_deterministic_and_follows_a_cell_shift(dev):
+    rng = np.random.default_rng(4)
+    n, L, cpd = 2000, 1.0, 8
+    pos = rng.random((n, 3)).astype(np.float32)
+    a1, _ = far_gpu(pos, L, cpd, 1e-3, dev, p=6, gm=1.0 / n)
+    a2, _ = far_gpu(pos, L, cpd, 1e-3, dev, p=6, gm=1.0 / n)
+    assert np.array_equal(a1, a2)
+    # a whole-cell shift by a power-of-two fraction of the box moves the far field along
+    shifted = np.mod(pos.astype(np.float64) + np.array([3, 1, 6]) / cpd, L).astype(np.float32)
+    a3, _ = far_gpu(shifted, L, cpd, 1e-3, dev, p=6, gm=1.0 / n)
+    scale = np.abs(a1).max()
+    assert np.abs(a3 - a1).max() <= 1e-5 * scale
+
+
+def test_far_argument_errors(dev):
+    from paper_2110_11398_gb300 import NearField, NFError
+    box = synth.tiny()
+    nf = NearField(box.L, box.cpd, box.eps, capacity=box.n, device=dev)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    with pytest.raises(NFError, match="NF_ESTATE"):
+        nf.far()
+    with pytest.raises(NFError, match="NF_EINVAL"):
+        nf.far_init(9)
+    with pytest.raises(NFError, match="NF_EINVAL"):
+        nf.far_init(0)
+    nf.close()
+    nb = NearField([1.0, 1.0], [5, 7], [1e-3, 1e-3], capacity=100, device=dev)
+    with pytest.raises(NFError, match="NF_EINVAL"):
+        nb.far_init(4)
+    nb.close()
