@@ -12,6 +12,16 @@
 //                           out; Ewald sum with a uniform background, |q| <= 2p
 //   Taylor        T_k(c)  = sum_c' sum_m (-1)^|m| / m!  D_{k+m}(c - c') M_m(c')
 //   acceleration  a(y)    = grad_y sum_k T_k y^k / k!   (times (CPD / L)^2)
+// Away from its sources the tensor is harmonic: D_{q+2x} + D_{q+2y} + D_{q+2z}
+// = 0 for |q| >= 1 (4 pi / CPD^3 for q = 0, the background). Hence (i) a
+// multipole term with x-exponent >= 2 equals minus the same term moved to
+// m - 2x + 2y and m - 2x + 2z, so the weighted multipoles W_m = (-1)^|m|/m! M_m
+// fold down to the 2l+1 per order with x-exponent <= 1 ("reduced" set); and
+// (ii) only the reduced T_k need the convolution, the others following from
+// T_k = -T_{k-2x+2y} - T_{k-2x+2z} (plus 4 pi M_tot / CPD^3 for k = (2,0,0)).
+// With p = 8 that is 81 x 81 products per frequency instead of 165 x 165,
+// 162 transforms per step instead of 330, and the tensor is stored only for
+// x-exponents <= 2.
 // The tensor is split as in Ewald's method: d^q [erfc(alpha r)/r] summed in
 // real space over the few lattice vectors it reaches (on the host, once), and
 // the rest, (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q, written straight into
@@ -55,17 +65,23 @@ struct MultiIndex {
 };
 
 struct FarState {
-    int p = 0, P = 0, np = 0, nq = 0;
+    int p = 0, P = 0, np = 0, nr = 0, nd = 0;
     double alpha = 0.0;
     int64_t ncell = 0, nfreq = 0;
-    double *M = nullptr;             // [np][ncell] multipoles, then reused for T
-    cufftDoubleComplex *Mh = nullptr;  // [np][nfreq]
-    cufftDoubleComplex *Th = nullptr;  // [np][nfreq]
-    cufftDoubleComplex *Dh = nullptr;  // [nq][nfreq]
-    int *mabc = nullptr;             // [3][np] multi-indices of order <= p (device)
-    int *conv_add = nullptr;         // [np][np]: position of k + m among the order-2p indices
-    double *conv_coef = nullptr;     // [np]: (-1)^|m| / m!
-    int *tay = nullptr;              // [4][ntay]: Taylor-gradient table (see k_far_taylor)
+    double *W = nullptr;               // [nr][ncell] reduced weighted multipoles, then the reduced T
+    cufftDoubleComplex *Wh = nullptr;  // [nr][nfreq]
+    cufftDoubleComplex *Th = nullptr;  // [nr][nfreq]
+    cufftDoubleComplex *Dh = nullptr;  // [nd][nfreq] tensor, x-exponent <= 2
+    int *mabc = nullptr;               // [3][np] all multi-indices of order <= p
+    double *coef = nullptr;            // [np] (-1)^|m| / m!
+    int *fold = nullptr;               // [3][nfold] W[d1] -= W[s], W[d2] -= W[s], in order
+    int nfold = 0;
+    int *red = nullptr;                // [nr] position (among the np) of each reduced index
+    int *conv_add = nullptr;           // [nr][nr] position of k + m among the stored tensor components
+    int *recon = nullptr;              // [3][nrec] T[k] = -T[s1] - T[s2], in order (k = (2,0,0) first)
+    int nrec = 0;
+    int k200 = -1;                     // position of (2,0,0) (gets the background term)
+    int *tay = nullptr;                // [4][ntay] Taylor-gradient table (see k_far_taylor)
     int ntay = 0;
     cufftHandle r2c = 0, c2r = 0;
     bool r2c_ok = false, c2r_ok = false;
@@ -144,8 +160,8 @@ void cartesian_derivs(const double v[3], const double *h, const MultiIndex &mi,
 // and each cell is summed by one thread in a fixed order, so the result does
 // not depend on the thread count.
 void real_space_part(int P, int R, double alpha, double r_cut, const MultiIndex &mq,
-                     std::vector<int64_t> &cells, std::vector<double> &vals) {
-    const int nq = mq.size();
+                     const std::vector<int> &keep, std::vector<int64_t> &cells, std::vector<double> &vals) {
+    const int nq = mq.size(), nk = (int)keep.size();
     const int smax = (int)std::ceil(r_cut);
     struct Vec { int64_t cell; int x, y, z; };
     std::vector<Vec> vecs;
@@ -163,14 +179,15 @@ void real_space_part(int P, int R, double alpha, double r_cut, const MultiIndex 
     for (size_t i = 0; i < vecs.size(); ++i)
         if (i == 0 || vecs[i].cell != vecs[i - 1].cell) { first.push_back(i); cells.push_back(vecs[i].cell); }
     first.push_back(vecs.size());
-    vals.assign(cells.size() * (size_t)nq, 0.0);
+    vals.assign(cells.size() * (size_t)nk, 0.0);
     const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     std::vector<std::thread> th;
     for (unsigned t = 0; t < nt; ++t)
         th.emplace_back([&, t]() {
-            std::vector<double> H;
+            std::vector<double> H, full(nq);
             double h[64];
-            for (size_t g = t; g < cells.size(); g += nt)
+            for (size_t g = t; g < cells.size(); g += nt) {
+                std::fill(full.begin(), full.end(), 0.0);
                 for (size_t i = first[g]; i < first[g + 1]; ++i) {
                     const Vec &v = vecs[i];
                     const double sv[3] = {(double)v.x, (double)v.y, (double)v.z};
@@ -178,8 +195,10 @@ void real_space_part(int P, int R, double alpha, double r_cut, const MultiIndex 
                     const bool near = std::abs(v.x) <= R && std::abs(v.y) <= R && std::abs(v.z) <= R;
                     if (near) radial_minus_erf(r, alpha, mq.n, h);
                     else radial_erfc(r, alpha, mq.n, h);
-                    cartesian_derivs(sv, h, mq, H, vals.data() + g * (size_t)nq);
+                    cartesian_derivs(sv, h, mq, H, full.data());
                 }
+                for (int k = 0; k < nk; ++k) vals[g * (size_t)nk + k] = full[keep[k]];
+            }
         });
     for (auto &x : th) x.join();
 }
@@ -242,15 +261,18 @@ __global__ void k_far_longrange(cufftDoubleComplex *__restrict__ Dh, int P, int6
 // particle-major so that a warp reading one particle's powers hits distinct
 // banks or one broadcast); thread t then owns components t and t + 128 and
 // sums mass * x^a y^b z^c over the tile in FP32, folded into an FP64 total
-// per tile.
+// per tile. The cell's W_m = coef_m M_m are then folded down to the reduced
+// set (one thread, in the table's order) and written component-major.
 constexpr int kFarThreads = 128;
 constexpr int kFarMaxP = 8;
 
 __global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
     const float4 *__restrict__ sorted, const int *__restrict__ cell_start, int64_t ncell, int p, int np,
-    const int *__restrict__ mabc, double *__restrict__ M) {
+    const int *__restrict__ mabc, const double *__restrict__ coef, const int *__restrict__ fold, int nfold,
+    const int *__restrict__ red, int nr, double *__restrict__ W) {
     __shared__ float pw[3][kFarThreads][kFarMaxP + 1];
     __shared__ float ms[kFarThreads];
+    __shared__ double Ws[2 * kFarThreads];
     const int t = threadIdx.x;
     const int i0 = t, i1 = t + kFarThreads;
     int a0 = 0, b0 = 0, c0 = 0, a1 = 0, b1 = 0, c1 = 0;
@@ -282,39 +304,48 @@ __global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
             acc0 += (double)f0;
             acc1 += (double)f1;
         }
-        if (i0 < np) M[(int64_t)i0 * ncell + cell] = acc0;
-        if (i1 < np) M[(int64_t)i1 * ncell + cell] = acc1;
+        __syncthreads();
+        if (i0 < np) Ws[i0] = coef[i0] * acc0;
+        if (i1 < np) Ws[i1] = coef[i1] * acc1;
+        __syncthreads();
+        if (t == 0)
+            for (int f = 0; f < nfold; ++f) {
+                const double v = Ws[fold[f]];
+                Ws[fold[nfold + f]] -= v;
+                Ws[fold[2 * nfold + f]] -= v;
+            }
+        __syncthreads();
+        for (int r = t; r < nr; r += kFarThreads) W[(int64_t)r * ncell + cell] = Ws[red[r]];
     }
 }
 
-// Per-frequency products T_k(w) = sum_m coef_m D_{k+m}(w) M_m(w): a block
-// takes 32 consecutive frequencies (one per lane); coef_m M_m(w) is staged in
-// shared memory; warp y of the block computes k = y, y + blockDim.y, ...
+// Per-frequency products T_k(w) = sum_m D_{k+m}(w) W_m(w) over the reduced
+// k and m: a block takes 32 consecutive frequencies (one per lane); W_m(w) is
+// staged in shared memory; warp y of the block computes k = y, y + blockDim.y, ...
 __global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
-                               const cufftDoubleComplex *__restrict__ Mh,
-                               cufftDoubleComplex *__restrict__ Th, int64_t nfreq, int np,
-                               const int *__restrict__ add, const double *__restrict__ coef) {
-    extern __shared__ double2 cm[];   // [np][32]
+                               const cufftDoubleComplex *__restrict__ Wh,
+                               cufftDoubleComplex *__restrict__ Th, int64_t nfreq, int nr,
+                               const int *__restrict__ add) {
+    extern __shared__ double2 cm[];   // [nr][32]
     const int lane = threadIdx.x, wy = threadIdx.y, ny = blockDim.y;
     for (int64_t f0 = (int64_t)blockIdx.x * 32; f0 < nfreq; f0 += (int64_t)gridDim.x * 32) {
         const int64_t f = f0 + lane;
         const bool ok = f < nfreq;
         __syncthreads();
-        for (int m = wy; m < np; m += ny) {
+        for (int m = wy; m < nr; m += ny) {
             double2 v = make_double2(0.0, 0.0);
             if (ok) {
-                const cufftDoubleComplex x = Mh[(int64_t)m * nfreq + f];
-                const double cf = coef[m];
-                v = make_double2(cf * x.x, cf * x.y);
+                const cufftDoubleComplex x = Wh[(int64_t)m * nfreq + f];
+                v = make_double2(x.x, x.y);
             }
             cm[m * 32 + lane] = v;
         }
         __syncthreads();
-        for (int k = wy; k < np; k += ny) {
+        for (int k = wy; k < nr; k += ny) {
             double re = 0.0, im = 0.0;
-            const int *ak = add + (int64_t)k * np;
+            const int *ak = add + (int64_t)k * nr;
             if (ok) {
-                for (int m = 0; m < np; ++m) {
+                for (int m = 0; m < nr; ++m) {
                     const cufftDoubleComplex d = Dh[(int64_t)__ldg(&ak[m]) * nfreq + f];
                     const double2 x = cm[m * 32 + lane];
                     re = fma(d.x, x.x, fma(-d.y, x.y, re));
@@ -326,21 +357,27 @@ __global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
     }
 }
 
-// Taylor gradient at every particle: one block per cell; the cell's T_k
-// (scaled to box units) are staged in shared memory as floats; each thread
-// takes a particle y and sums, over |j| <= p - 1,
+// Taylor gradient at every particle: one block per cell. The cell's reduced
+// T (inverse transform / CPD^3) are completed to all |k| <= p in FP64 by the
+// harmonic relation, with the background term 4 pi M_tot / CPD^3 on (2,0,0)
+// (M_tot is the zero-frequency value of W_0), scaled to box units and staged
+// as floats; each thread takes a particle y and sums, over |j| <= p - 1,
 //   (y^j / j!) (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}).
 // tay[0..3][i] = (a, b, c) of j and, packed, the positions of j + e_x,
 // j + e_y, j + e_z among the order-p indices (10 bits each).
 __global__ void __launch_bounds__(kFarThreads) k_far_taylor(
     const float4 *__restrict__ sorted, const int *__restrict__ cell_start, const int *__restrict__ perm,
-    const double *__restrict__ T, int64_t ncell, int p, int np, const int *__restrict__ tay, int ntay,
-    double scale, float *__restrict__ acc, int accumulate) {
-    __shared__ float Ts[kFarThreads * 2];
+    const double *__restrict__ Tr, int64_t ncell, int p, int np, const int *__restrict__ red, int nr,
+    const int *__restrict__ recon, int nrec, int k200, const cufftDoubleComplex *__restrict__ w0_dc,
+    const int *__restrict__ tay, int ntay, double inv_n, double inv_h2, float *__restrict__ acc,
+    int accumulate) {
+    __shared__ double Td[2 * kFarThreads];
+    __shared__ float Ts[2 * kFarThreads];
     __shared__ int tj[4][kFarThreads];
     const int t = threadIdx.x;
     for (int i = t; i < ntay; i += kFarThreads)
         for (int r = 0; r < 4; ++r) tj[r][i] = tay[r * ntay + i];
+    const double bg = 4.0 * M_PI * w0_dc->x * inv_n;   // 4 pi M_tot / CPD^3
     float inv_fact[kFarMaxP + 1];
     inv_fact[0] = 1.f;
     for (int j = 1; j <= kFarMaxP; ++j) inv_fact[j] = inv_fact[j - 1] / (float)j;
@@ -348,7 +385,17 @@ __global__ void __launch_bounds__(kFarThreads) k_far_taylor(
         const int s = cell_start[cell], e = cell_start[cell + 1];
         if (s == e) continue;   // uniform over the block
         __syncthreads();
-        for (int i = t; i < np; i += kFarThreads) Ts[i] = (float)(T[(int64_t)i * ncell + cell] * scale);
+        for (int r = t; r < nr; r += kFarThreads) Td[red[r]] = Tr[(int64_t)r * ncell + cell] * inv_n;
+        __syncthreads();
+        if (t == 0)
+            for (int i = 0; i < nrec; ++i) {
+                const int k = recon[i];
+                double v = -Td[recon[nrec + i]] - Td[recon[2 * nrec + i]];
+                if (k == k200) v += bg;
+                Td[k] = v;
+            }
+        __syncthreads();
+        for (int i = t; i < np; i += kFarThreads) Ts[i] = (float)(Td[i] * inv_h2);
         __syncthreads();
         for (int j = s + t; j < e; j += kFarThreads) {
             const float4 r = sorted[j];
@@ -406,7 +453,7 @@ int grid_blocks(int64_t n, int threads, int sm_count, int per_sm) {
 void far_release(Ctx *c) {
     FarState *f = c->far;
     if (!f) return;
-    void *bufs[] = {f->M, f->Mh, f->Th, f->Dh, f->mabc, f->conv_add, f->conv_coef, f->tay};
+    void *bufs[] = {f->W, f->Wh, f->Th, f->Dh, f->mabc, f->coef, f->fold, f->red, f->conv_add, f->recon, f->tay};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (f->r2c_ok) cufftDestroy(f->r2c);
@@ -432,7 +479,6 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
     mp.build(order);
     mq.build(2 * order);
     f->np = mp.size();
-    f->nq = mq.size();
     // splitting: the real-space part reaches r < (6.5 + q/4)/alpha cells and the
     // Fourier part |k| < (13 + q/2) alpha; alpha = max(0.5, 3.5/P) keeps both small
     f->alpha = std::max(0.5, 3.5 / P);
@@ -449,9 +495,17 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
         return r == CUFFT_ALLOC_FAILED ? NF_ENOMEM : NF_ECUDA;
     };
     cudaError_t e;
-    // index tables
+    // ---- index tables
+    std::vector<int> red, red_of(f->np, -1);
+    for (int i = 0; i < f->np; ++i)
+        if (mp.a[i] <= 1) { red_of[i] = (int)red.size(); red.push_back(i); }
+    f->nr = (int)red.size();
+    std::vector<int> stored, stored_of(mq.size(), -1);   // tensor components kept: x-exponent <= 2
+    for (int i = 0; i < mq.size(); ++i)
+        if (mq.a[i] <= 2) { stored_of[i] = (int)stored.size(); stored.push_back(i); }
+    f->nd = (int)stored.size();
     {
-        std::vector<int> mabc(3 * (size_t)f->np), add((size_t)f->np * f->np), qabc(3 * (size_t)f->nq);
+        std::vector<int> mabc(3 * (size_t)f->np), add((size_t)f->nr * f->nr), dabc(3 * (size_t)f->nd);
         std::vector<double> coef(f->np);
         for (int i = 0; i < f->np; ++i) {
             mabc[i] = mp.a[i]; mabc[f->np + i] = mp.b[i]; mabc[2 * f->np + i] = mp.c[i];
@@ -461,11 +515,43 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             for (int x = 2; x <= mp.c[i]; ++x) fac *= x;
             coef[i] = (((mp.a[i] + mp.b[i] + mp.c[i]) & 1) ? -1.0 : 1.0) / fac;
         }
-        for (int k = 0; k < f->np; ++k)
-            for (int m = 0; m < f->np; ++m)
-                add[(size_t)k * f->np + m] = mq.at(mp.a[k] + mp.a[m], mp.b[k] + mp.b[m], mp.c[k] + mp.c[m]);
-        for (int i = 0; i < f->nq; ++i) {
-            qabc[i] = mq.a[i]; qabc[f->nq + i] = mq.b[i]; qabc[2 * f->nq + i] = mq.c[i];
+        // fold of W: x-exponent from p down to 2
+        std::vector<int> fs, fd1, fd2;
+        for (int a = order; a >= 2; --a)
+            for (int i = 0; i < f->np; ++i)
+                if (mp.a[i] == a) {
+                    fs.push_back(i);
+                    fd1.push_back(mp.at(a - 2, mp.b[i] + 2, mp.c[i]));
+                    fd2.push_back(mp.at(a - 2, mp.b[i], mp.c[i] + 2));
+                }
+        f->nfold = (int)fs.size();
+        std::vector<int> fold;
+        fold.insert(fold.end(), fs.begin(), fs.end());
+        fold.insert(fold.end(), fd1.begin(), fd1.end());
+        fold.insert(fold.end(), fd2.begin(), fd2.end());
+        // completion of T: x-exponent from 2 up to p
+        std::vector<int> rk, rs1, rs2;
+        for (int a = 2; a <= order; ++a)
+            for (int i = 0; i < f->np; ++i)
+                if (mp.a[i] == a) {
+                    rk.push_back(i);
+                    rs1.push_back(mp.at(a - 2, mp.b[i] + 2, mp.c[i]));
+                    rs2.push_back(mp.at(a - 2, mp.b[i], mp.c[i] + 2));
+                }
+        f->nrec = (int)rk.size();
+        f->k200 = order >= 2 ? mp.at(2, 0, 0) : -1;
+        std::vector<int> recon;
+        recon.insert(recon.end(), rk.begin(), rk.end());
+        recon.insert(recon.end(), rs1.begin(), rs1.end());
+        recon.insert(recon.end(), rs2.begin(), rs2.end());
+        for (int k = 0; k < f->nr; ++k)
+            for (int m = 0; m < f->nr; ++m) {
+                const int ik = red[k], im = red[m];
+                add[(size_t)k * f->nr + m] =
+                    stored_of[mq.at(mp.a[ik] + mp.a[im], mp.b[ik] + mp.b[im], mp.c[ik] + mp.c[im])];
+            }
+        for (int i = 0; i < f->nd; ++i) {
+            dabc[i] = mq.a[stored[i]]; dabc[f->nd + i] = mq.b[stored[i]]; dabc[2 * f->nd + i] = mq.c[stored[i]];
         }
         // Taylor gradient: every j with |j| <= p - 1
         std::vector<int> ja, jb, jc, jp;
@@ -481,38 +567,38 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
         tay.insert(tay.end(), jb.begin(), jb.end());
         tay.insert(tay.end(), jc.begin(), jc.end());
         tay.insert(tay.end(), jp.begin(), jp.end());
-        if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->conv_add, add)) ||
-            (e = upload(&f->conv_coef, coef)) || (e = upload(&f->tay, tay)))
+        if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->coef, coef)) || (e = upload(&f->fold, fold)) ||
+            (e = upload(&f->red, red)) || (e = upload(&f->conv_add, add)) || (e = upload(&f->recon, recon)) ||
+            (e = upload(&f->tay, tay)))
             return cuda_err(e, "tables");
-        int *qa = nullptr;
-        if ((e = upload(&qa, qabc))) return cuda_err(e, "tables");
-        // real-space part (host), scattered into a zeroed FP64 grid
+        int *da = nullptr;
+        if ((e = upload(&da, dabc))) return cuda_err(e, "tables");
+        // ---- real-space part of the tensor (host), scattered into a zeroed FP64 grid
         std::vector<int64_t> cells;
         std::vector<double> vals;
-        real_space_part(P, c->R, f->alpha, r_cut, mq, cells, vals);
+        real_space_part(P, c->R, f->alpha, r_cut, mq, stored, cells, vals);
         double *grid = nullptr, *dvals = nullptr;
         int64_t *dcells = nullptr;
-        if ((e = dmalloc(&f->Dh, (size_t)f->nq * f->nfreq))) { cudaFree(qa); return cuda_err(e, "tensor"); }
-        if ((e = dmalloc(&grid, (size_t)f->nq * f->ncell)) || (e = upload(&dvals, vals)) || (e = upload(&dcells, cells))) {
-            cudaFree(qa); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+        if ((e = dmalloc(&f->Dh, (size_t)f->nd * f->nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
+        if ((e = dmalloc(&grid, (size_t)f->nd * f->ncell)) || (e = upload(&dvals, vals)) || (e = upload(&dcells, cells))) {
+            cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
             return cuda_err(e, "tensor");
         }
-        e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nq * f->ncell, s);
+        e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nd * f->ncell, s);
         if (!e) {
-            k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nq, 256, c->sm_count, 8), 256, 0, s>>>(
-                dvals, dcells, (int64_t)cells.size(), f->nq, f->ncell, grid);
+            k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nd, 256, c->sm_count, 8), 256, 0, s>>>(
+                dvals, dcells, (int64_t)cells.size(), f->nd, f->ncell, grid);
             e = cudaGetLastError();
         }
-        // forward transforms of the tensor, a few components per plan execution
         // the tensor's components are transformed 64 at a time, the rest by a
         // second plan: chunk starts stay at even component offsets, which
         // keeps them 16-byte aligned as cuFFT requires of its data
         cufftHandle plan = 0, plan_rest = 0;
         int dims[3] = {P, P, P};
-        const int chunk = 64, rest = f->nq % chunk;
+        const int chunk = 64, rest = f->nd % chunk;
         const char *stage = "tensor transform: plan";
         cufftResult fr = CUFFT_SUCCESS;
-        if (!e && f->nq >= chunk)
+        if (!e && f->nd >= chunk)
             fr = cufftPlanMany(&plan, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, chunk);
         if (!e && fr == CUFFT_SUCCESS && rest)
             fr = cufftPlanMany(&plan_rest, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, rest);
@@ -521,33 +607,33 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             if (plan) fr = cufftSetStream(plan, s);
             if (fr == CUFFT_SUCCESS && plan_rest) fr = cufftSetStream(plan_rest, s);
         }
-        for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nq; q0 += chunk) {
+        for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nd; q0 += chunk) {
             stage = "tensor transform: exec";
-            fr = cufftExecD2Z(q0 + chunk <= f->nq ? plan : plan_rest, grid + (size_t)q0 * f->ncell,
+            fr = cufftExecD2Z(q0 + chunk <= f->nd ? plan : plan_rest, grid + (size_t)q0 * f->ncell,
                               f->Dh + (size_t)q0 * f->nfreq);
         }
         if (!e && fr == CUFFT_SUCCESS) {
             k_far_longrange<<<grid_blocks(f->nfreq, 128, c->sm_count, 8), 128, 0, s>>>(
-                f->Dh, P, f->nfreq, f->nq, qa, qa + f->nq, qa + 2 * f->nq, f->alpha, k_cut);
+                f->Dh, P, f->nfreq, f->nd, da, da + f->nd, da + 2 * f->nd, f->alpha, k_cut);
             e = cudaGetLastError();
         }
         if (!e) e = cudaStreamSynchronize(s);
         if (plan) cufftDestroy(plan);
         if (plan_rest) cufftDestroy(plan_rest);
-        cudaFree(qa); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+        cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
         if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
         if (e) return cuda_err(e, "tensor");
     }
-    // per-step buffers and plans
-    if ((e = dmalloc(&f->M, (size_t)f->np * f->ncell)) || (e = dmalloc(&f->Mh, (size_t)f->np * f->nfreq)) ||
-        (e = dmalloc(&f->Th, (size_t)f->np * f->nfreq)))
+    // ---- per-step buffers and plans (reduced components)
+    if ((e = dmalloc(&f->W, (size_t)f->nr * f->ncell)) || (e = dmalloc(&f->Wh, (size_t)f->nr * f->nfreq)) ||
+        (e = dmalloc(&f->Th, (size_t)f->nr * f->nfreq)))
         return cuda_err(e, "buffers");
     int dims[3] = {P, P, P};
     cufftResult fr = cufftPlanMany(&f->r2c, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq,
-                                   CUFFT_D2Z, f->np);
+                                   CUFFT_D2Z, f->nr);
     if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
     f->r2c_ok = true;
-    fr = cufftPlanMany(&f->c2r, 3, dims, nullptr, 1, (int)f->nfreq, nullptr, 1, (int)f->ncell, CUFFT_Z2D, f->np);
+    fr = cufftPlanMany(&f->c2r, 3, dims, nullptr, 1, (int)f->nfreq, nullptr, 1, (int)f->ncell, CUFFT_Z2D, f->nr);
     if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
     f->c2r_ok = true;
     return NF_OK;
@@ -559,26 +645,28 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
     FarState *f = c->far;
     const BoxDev &B = c->boxes_h[0];
     k_far_multipoles<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->M);
+        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->coef, f->fold, f->nfold, f->red, f->nr, f->W);
     c->launches += 1;
     cudaError_t e = cudaGetLastError();
     if (e) return e;
-    if (cufftSetStream(f->r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(f->r2c, f->M, f->Mh) != CUFFT_SUCCESS)
+    if (cufftSetStream(f->r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(f->r2c, f->W, f->Wh) != CUFFT_SUCCESS)
         return cudaErrorUnknown;
+    // W_0 is reduced component 0: its zero-frequency value is the total mass,
+    // read by the Taylor kernel for the background term (the inverse
+    // transform below overwrites Th only)
     const int ny = 8;
-    const size_t smem = sizeof(double2) * 32 * (size_t)f->np;
+    const size_t smem = sizeof(double2) * 32 * (size_t)f->nr;
     e = cudaFuncSetAttribute(k_far_convolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
     k_far_convolve<<<grid_blocks(f->nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
-        f->Dh, f->Mh, f->Th, f->nfreq, f->np, f->conv_add, f->conv_coef);
+        f->Dh, f->Wh, f->Th, f->nfreq, f->nr, f->conv_add);
     c->launches += 1;
     if ((e = cudaGetLastError())) return e;
-    if (cufftSetStream(f->c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(f->c2r, f->Th, f->M) != CUFFT_SUCCESS)
+    if (cufftSetStream(f->c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(f->c2r, f->Th, f->W) != CUFFT_SUCCESS)
         return cudaErrorUnknown;
-    // T = inverse transform / P^3; acceleration in box units = cell units * inv_h2
-    const double scale = B.inv_h2_d / (double)f->ncell;
     k_far_taylor<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, c->perm, f->M, f->ncell, f->p, f->np, f->tay, f->ntay, scale, acc, accumulate);
+        c->sorted, c->cell_start, c->perm, f->W, f->ncell, f->p, f->np, f->red, f->nr, f->recon, f->nrec,
+        f->k200, f->Wh, f->tay, f->ntay, 1.0 / (double)f->ncell, B.inv_h2_d, acc, accumulate);
     c->launches += 1;
     return cudaGetLastError();
 }
