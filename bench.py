@@ -337,6 +337,16 @@ class PlainRunner:
         self.dens = torch.empty(box.n, dtype=torch.float32, device=dev) if self.kde_b else None
         self.flops_per_pair = (FLOPS_PER_PAIR + (SPLINE_EXTRA_FLOPS if self.law == "spline" else 0)
                                + (KDE_EXTRA_FLOPS if self.kde_b else 0))
+        self.far_order = getattr(args, "far", 0) or 0
+        self.far_out = None
+        self.far_init_s = None
+        if self.far_order:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.nf.far_init(self.far_order)
+            torch.cuda.synchronize()
+            self.far_init_s = time.perf_counter() - t0
+            self.far_out = torch.empty_like(self.out)
         self.kdk = getattr(args, "kdk", False)
         if self.kdk:
             # synthetic velocities, N(0, 1) in units of the mean spacing per unit
@@ -357,6 +367,8 @@ class PlainRunner:
             self.nf.accel_density(self.kde_b, out=self.out, density=self.dens)
         else:
             self.nf.accel(out=self.out)
+        if self.far_order:
+            self.nf.far(out=self.far_out)
 
     def stats(self):
         return self.nf.stats()
@@ -372,6 +384,9 @@ class PlainRunner:
         if self.kdk:
             cfg["step"] = "kick-drift-kick (half kick, drift, re-bin, accelerations, half kick)"
             cfg["dt"] = self.dt
+        if self.far_order:
+            cfg["far_order"] = self.far_order
+            cfg["step"] = "bin, near-field accelerations, far-field accelerations (order %d)" % self.far_order
         return cfg
 
     e2e_note = "nf_accel_host: H2D positions, bin, accelerations, D2H"
@@ -380,12 +395,37 @@ class PlainRunner:
         torch = self.torch
         if self.kdk:
             return self._e2e_kdk(reps)
+        if self.far_order:
+            return self._e2e_far(reps)
         hpos = torch.from_numpy(self.box.pos).pin_memory().numpy()
         hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory().numpy()
         self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
         t0 = time.perf_counter()
         for _ in range(reps):
             self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
+        return (time.perf_counter() - t0) / reps, int(hpos.nbytes), int(hacc.nbytes)
+
+    def _e2e_far(self, reps):
+        """Near + far field on host buffers: positions in, the total
+        acceleration (near + far, summed on the device) back, every step."""
+        torch = self.torch
+        self.e2e_note = "H2D positions, bin, near field, far field added on, D2H total acceleration"
+        hpos = torch.from_numpy(self.box.pos).pin_memory()
+        hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory()
+        pos = torch.empty_like(self.pos)
+
+        def once():
+            pos.copy_(hpos, non_blocking=True)
+            self.nf.bin(pos, gm=self.box.gm)
+            self.nf.accel(out=self.out)
+            self.nf.far(out=self.out, accumulate=True)
+            hacc.copy_(self.out, non_blocking=True)
+            torch.cuda.synchronize()
+
+        once()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
         return (time.perf_counter() - t0) / reps, int(hpos.nbytes), int(hacc.nbytes)
 
     def _e2e_kdk(self, reps):
@@ -655,13 +695,15 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    pair_ms, bin_ms = [], []
+    pair_ms, bin_ms, far_ms, far_conv_ms = [], [], [], []
     e0.record(stream)
     for _ in range(args.steps):
         run.step()
         st = run.stats()
         pair_ms.append(st["pair_ms"])
         bin_ms.append(st["bin_ms"])
+        far_ms.append(st.get("far_ms", 0.0))
+        far_conv_ms.append(st.get("far_conv_ms", 0.0))
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -707,6 +749,19 @@ def run_ours(args):
                 "bytes_per_launch": bin_bytes}
     roof_bin["frac"] = roof_bin["achieved"] / roof_bin["peak"]
     extra = {}
+    if getattr(run, "far_order", 0):
+        P, p = run.box.cpd, run.far_order
+        nfreq = P * P * (P // 2 + 1)
+        nr = (p + 1) ** 2                      # reduced multipoles / Taylor coefficients
+        conv_flops = 8.0 * nfreq * nr * nr     # complex FP64 multiply-add per (k, m, frequency)
+        conv_ms = float(np.mean(far_conv_ms))
+        fp64_peak = fp64_peak_tflops(props.multi_processor_count, sm_max)
+        extra["far_field"] = {
+            "order": p, "init_s": run.far_init_s, "ms_per_step": float(np.mean(far_ms)),
+            "share_of_step": float(np.mean(far_ms)) / ms_per_step,
+            "convolve": {"bound": "fp64", "ms": conv_ms, "flops_per_launch": conv_flops,
+                         "achieved": conv_flops / (conv_ms / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": conv_flops / (conv_ms / 1e3) / 1e12 / fp64_peak}}
     if isinstance(run, AdjointRunner):
         fwd = float(np.mean(run.fwd_ms[-args.steps:]))
         extra["forward_pair_ms"] = fwd
@@ -785,6 +840,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp64"])
     ap.add_argument("--softening", default="plummer", choices=["plummer", "spline"])
     ap.add_argument("--kde", action="store_true", help="also compute the kernel density estimate")
+    ap.add_argument("--far", type=int, default=0, metavar="P",
+                    help="also compute the far field of order P each step (one-box workloads)")
     ap.add_argument("--kdk", action="store_true",
                     help="time full leapfrog steps (kick, drift, re-bin, accelerations, kick)")
     ap.add_argument("--sinks-per-lane", type=int, default=0)

@@ -88,6 +88,8 @@ typedef struct nf_stats {
     double  pair_ms;         /* device time of the last pair (or adjoint) kernel */
     int64_t kernel_launches; /* kernels launched by this context so far, graph
                                 replays counted kernel by kernel */
+    double  far_ms;          /* device time of the last nf_compute_far (0 if none) */
+    double  far_conv_ms;     /* of which the per-frequency tensor products */
 } nf_stats;
 
 /* Launch shape of the pair kernels. sinks_per_lane in {1,2,4}; warps_per_block

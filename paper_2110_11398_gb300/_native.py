@@ -32,7 +32,8 @@ class nf_stats(ctypes.Structure):
                 ("interactions", ctypes.c_int64), ("max_occupancy", ctypes.c_int64),
                 ("n_items", ctypes.c_int64), ("momentum", ctypes.c_double * 3),
                 ("abs_momentum", ctypes.c_double), ("bin_ms", ctypes.c_double),
-                ("pair_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("pair_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("far_ms", ctypes.c_double), ("far_conv_ms", ctypes.c_double)]
 
 
 class nf_tuning(ctypes.Structure):

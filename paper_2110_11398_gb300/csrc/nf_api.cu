@@ -72,7 +72,8 @@ void release(Ctx *c) {
     if (c->g_vjp.exec) cudaGraphExecDestroy(c->g_vjp.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     far_release(c);
-    cudaEvent_t evs[] = {c->ev_bin0, c->ev_bin1, c->ev_pair0, c->ev_pair1};
+    cudaEvent_t evs[] = {c->ev_bin0, c->ev_bin1, c->ev_pair0, c->ev_pair1,
+                         c->ev_far[0], c->ev_far[1], c->ev_far[2], c->ev_far[3]};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     if (prev >= 0) cudaSetDevice(prev);
@@ -543,8 +544,11 @@ int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream) {
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (c->n == 0) return NF_OK;
+    for (cudaEvent_t &ev : c->ev_far)
+        if (!ev) NF_CK(c, cudaEventCreate(&ev));
     cudaError_t e = far_compute(c, acc, accumulate ? 1 : 0, s);
     if (e) return cuda_fail(c, e, "nf_compute_far");
+    c->have_far_time = 1;
     c->last_stream = s;
     return NF_OK;
 }
@@ -678,6 +682,12 @@ int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
     out->pair_ms = (c->have_pair_time && cudaEventElapsedTime(&ms, c->ev_pair0, c->ev_pair1) == cudaSuccess) ? ms : 0.0;
     cudaGetLastError();
     out->kernel_launches = c->launches;
+    out->far_ms = out->far_conv_ms = 0.0;
+    if (c->have_far_time) {
+        if (cudaEventElapsedTime(&ms, c->ev_far[0], c->ev_far[1]) == cudaSuccess) out->far_ms = ms;
+        if (cudaEventElapsedTime(&ms, c->ev_far[2], c->ev_far[3]) == cudaSuccess) out->far_conv_ms = ms;
+        cudaGetLastError();
+    }
     return NF_OK;
 }
 

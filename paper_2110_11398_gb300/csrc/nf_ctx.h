@@ -84,6 +84,8 @@ struct Ctx {
 
     // timing of the last binning / pair kernel, and the launch counter
     cudaEvent_t ev_bin0 = nullptr, ev_bin1 = nullptr, ev_pair0 = nullptr, ev_pair1 = nullptr;
+    cudaEvent_t ev_far[4] = {nullptr, nullptr, nullptr, nullptr};   // far step, convolution (start, end)
+    int have_far_time = 0;
     int64_t launches = 0;
     int have_bin_time = 0, have_pair_time = 0;
 

@@ -74,15 +74,13 @@ struct FarState {
     cufftDoubleComplex *Dh = nullptr;  // [nd][nfreq] tensor, x-exponent <= 2
     int *mabc = nullptr;               // [3][np] all multi-indices of order <= p
     double *coef = nullptr;            // [np] (-1)^|m| / m!
-    int *fold = nullptr;               // [3][nfold] W[d1] -= W[s], W[d2] -= W[s], in order
-    int nfold = 0;
-    int *red = nullptr;                // [nr] position (among the np) of each reduced index
+    // fold: reduced W_r = sum_e fval[e] * (coef M)[fcol[e]], e in [fptr[r], fptr[r+1])
+    int *fptr = nullptr, *fcol = nullptr;
+    double *fval = nullptr;
+    // completion: T_k = sum_e gval[e] * T_red[gcol[e]] + gbg[k] * (4 pi M_tot / CPD^3), k < np
+    int *gptr = nullptr, *gcol = nullptr;
+    double *gval = nullptr, *gbg = nullptr;
     int *conv_add = nullptr;           // [nr][nr] position of k + m among the stored tensor components
-    int *recon = nullptr;              // [3][nrec] T[k] = -T[s1] - T[s2], in order (k = (2,0,0) first)
-    int nrec = 0;
-    int k200 = -1;                     // position of (2,0,0) (gets the background term)
-    int *tay = nullptr;                // [4][ntay] Taylor-gradient table (see k_far_taylor)
-    int ntay = 0;
     cufftHandle r2c = 0, c2r = 0;
     bool r2c_ok = false, c2r_ok = false;
 };
@@ -262,14 +260,15 @@ __global__ void k_far_longrange(cufftDoubleComplex *__restrict__ Dh, int P, int6
 // banks or one broadcast); thread t then owns components t and t + 128 and
 // sums mass * x^a y^b z^c over the tile in FP32, folded into an FP64 total
 // per tile. The cell's W_m = coef_m M_m are then folded down to the reduced
-// set (one thread, in the table's order) and written component-major.
+// set by a fixed sparse map (one reduced component per thread) and written
+// component-major.
 constexpr int kFarThreads = 128;
 constexpr int kFarMaxP = 8;
 
 __global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
     const float4 *__restrict__ sorted, const int *__restrict__ cell_start, int64_t ncell, int p, int np,
-    const int *__restrict__ mabc, const double *__restrict__ coef, const int *__restrict__ fold, int nfold,
-    const int *__restrict__ red, int nr, double *__restrict__ W) {
+    const int *__restrict__ mabc, const double *__restrict__ coef, const int *__restrict__ fptr,
+    const int *__restrict__ fcol, const double *__restrict__ fval, int nr, double *__restrict__ W) {
     __shared__ float pw[3][kFarThreads][kFarMaxP + 1];
     __shared__ float ms[kFarThreads];
     __shared__ double Ws[2 * kFarThreads];
@@ -308,14 +307,11 @@ __global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
         if (i0 < np) Ws[i0] = coef[i0] * acc0;
         if (i1 < np) Ws[i1] = coef[i1] * acc1;
         __syncthreads();
-        if (t == 0)
-            for (int f = 0; f < nfold; ++f) {
-                const double v = Ws[fold[f]];
-                Ws[fold[nfold + f]] -= v;
-                Ws[fold[2 * nfold + f]] -= v;
-            }
-        __syncthreads();
-        for (int r = t; r < nr; r += kFarThreads) W[(int64_t)r * ncell + cell] = Ws[red[r]];
+        for (int r = t; r < nr; r += kFarThreads) {
+            double v = 0.0;
+            for (int q = fptr[r]; q < fptr[r + 1]; ++q) v = fma(fval[q], Ws[fcol[q]], v);
+            W[(int64_t)r * ncell + cell] = v;
+        }
     }
 }
 
@@ -357,68 +353,67 @@ __global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
     }
 }
 
+// Position of (a, b, c) among the multi-indices of order <= p (enumeration:
+// degree t, then c ascending, then b ascending).
+__host__ __device__ constexpr int mi_pos(int a, int b, int c) {
+    return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + c * (a + b + c + 1) - c * (c - 1) / 2 + b;
+}
+
 // Taylor gradient at every particle: one block per cell. The cell's reduced
 // T (inverse transform / CPD^3) are completed to all |k| <= p in FP64 by the
-// harmonic relation, with the background term 4 pi M_tot / CPD^3 on (2,0,0)
-// (M_tot is the zero-frequency value of W_0), scaled to box units and staged
-// as floats; each thread takes a particle y and sums, over |j| <= p - 1,
+// harmonic relation, a fixed sparse map (one component per thread) that also
+// carries the background term 4 pi M_tot / CPD^3 (M_tot is the
+// zero-frequency value of W_0), scaled to box units and staged as floats; each thread takes a particle y and sums, over |j| <= p - 1,
 //   (y^j / j!) (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}).
-// tay[0..3][i] = (a, b, c) of j and, packed, the positions of j + e_x,
-// j + e_y, j + e_z among the order-p indices (10 bits each).
+// The order is a template parameter, so the loops unroll with the
+// coefficient positions as constants and the powers of y in registers.
+template <int P>
 __global__ void __launch_bounds__(kFarThreads) k_far_taylor(
     const float4 *__restrict__ sorted, const int *__restrict__ cell_start, const int *__restrict__ perm,
-    const double *__restrict__ Tr, int64_t ncell, int p, int np, const int *__restrict__ red, int nr,
-    const int *__restrict__ recon, int nrec, int k200, const cufftDoubleComplex *__restrict__ w0_dc,
-    const int *__restrict__ tay, int ntay, double inv_n, double inv_h2, float *__restrict__ acc,
+    const double *__restrict__ Tr, int64_t ncell, int np, int nr, const int *__restrict__ gptr,
+    const int *__restrict__ gcol, const double *__restrict__ gval, const double *__restrict__ gbg,
+    const cufftDoubleComplex *__restrict__ w0_dc, double inv_n, double inv_h2, float *__restrict__ acc,
     int accumulate) {
-    __shared__ double Td[2 * kFarThreads];
+    __shared__ double Tred[2 * kFarThreads];
     __shared__ float Ts[2 * kFarThreads];
-    __shared__ int tj[4][kFarThreads];
     const int t = threadIdx.x;
-    for (int i = t; i < ntay; i += kFarThreads)
-        for (int r = 0; r < 4; ++r) tj[r][i] = tay[r * ntay + i];
     const double bg = 4.0 * M_PI * w0_dc->x * inv_n;   // 4 pi M_tot / CPD^3
-    float inv_fact[kFarMaxP + 1];
-    inv_fact[0] = 1.f;
-    for (int j = 1; j <= kFarMaxP; ++j) inv_fact[j] = inv_fact[j - 1] / (float)j;
     for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
         const int s = cell_start[cell], e = cell_start[cell + 1];
         if (s == e) continue;   // uniform over the block
         __syncthreads();
-        for (int r = t; r < nr; r += kFarThreads) Td[red[r]] = Tr[(int64_t)r * ncell + cell] * inv_n;
+        for (int r = t; r < nr; r += kFarThreads) Tred[r] = Tr[(int64_t)r * ncell + cell] * inv_n;
         __syncthreads();
-        if (t == 0)
-            for (int i = 0; i < nrec; ++i) {
-                const int k = recon[i];
-                double v = -Td[recon[nrec + i]] - Td[recon[2 * nrec + i]];
-                if (k == k200) v += bg;
-                Td[k] = v;
-            }
-        __syncthreads();
-        for (int i = t; i < np; i += kFarThreads) Ts[i] = (float)(Td[i] * inv_h2);
+        for (int k = t; k < np; k += kFarThreads) {
+            double v = gbg[k] * bg;
+            for (int q = gptr[k]; q < gptr[k + 1]; ++q) v = fma(gval[q], Tred[gcol[q]], v);
+            Ts[k] = (float)(v * inv_h2);
+        }
         __syncthreads();
         for (int j = s + t; j < e; j += kFarThreads) {
             const float4 r = sorted[j];
-            float px[kFarMaxP], py[kFarMaxP], pz[kFarMaxP];   // y^e / e!
+            float px[P], py[P], pz[P];   // y^e / e!
             px[0] = py[0] = pz[0] = 1.f;
-            for (int q = 1; q < p; ++q) {
-                px[q] = px[q - 1] * r.x;
-                py[q] = py[q - 1] * r.y;
-                pz[q] = pz[q - 1] * r.z;
-            }
-            for (int q = 1; q < p; ++q) {
-                px[q] *= inv_fact[q];
-                py[q] *= inv_fact[q];
-                pz[q] *= inv_fact[q];
+#pragma unroll
+            for (int q = 1; q < P; ++q) {
+                px[q] = px[q - 1] * r.x * (1.f / q);
+                py[q] = py[q - 1] * r.y * (1.f / q);
+                pz[q] = pz[q - 1] * r.z * (1.f / q);
             }
             float ax = 0.f, ay = 0.f, az = 0.f;
-            for (int i = 0; i < ntay; ++i) {
-                const float y = px[tj[0][i]] * py[tj[1][i]] * pz[tj[2][i]];
-                const int pk = tj[3][i];
-                ax = fmaf(y, Ts[pk & 1023], ax);
-                ay = fmaf(y, Ts[(pk >> 10) & 1023], ay);
-                az = fmaf(y, Ts[pk >> 20], az);
-            }
+#pragma unroll
+            for (int a = 0; a < P; ++a)
+#pragma unroll
+                for (int b = 0; a + b < P; ++b) {
+                    const float xy = px[a] * py[b];
+#pragma unroll
+                    for (int c = 0; a + b + c < P; ++c) {
+                        const float y = xy * pz[c];
+                        ax = fmaf(y, Ts[mi_pos(a + 1, b, c)], ax);
+                        ay = fmaf(y, Ts[mi_pos(a, b + 1, c)], ay);
+                        az = fmaf(y, Ts[mi_pos(a, b, c + 1)], az);
+                    }
+                }
             float *o = acc + 3 * (int64_t)perm[j];
             if (accumulate) {
                 o[0] += ax; o[1] += ay; o[2] += az;
@@ -453,7 +448,8 @@ int grid_blocks(int64_t n, int threads, int sm_count, int per_sm) {
 void far_release(Ctx *c) {
     FarState *f = c->far;
     if (!f) return;
-    void *bufs[] = {f->W, f->Wh, f->Th, f->Dh, f->mabc, f->coef, f->fold, f->red, f->conv_add, f->recon, f->tay};
+    void *bufs[] = {f->W, f->Wh, f->Th, f->Dh, f->mabc, f->coef, f->fptr, f->fcol, f->fval,
+                    f->gptr, f->gcol, f->gval, f->gbg, f->conv_add};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (f->r2c_ok) cufftDestroy(f->r2c);
@@ -515,35 +511,58 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             for (int x = 2; x <= mp.c[i]; ++x) fac *= x;
             coef[i] = (((mp.a[i] + mp.b[i] + mp.c[i]) & 1) ? -1.0 : 1.0) / fac;
         }
-        // fold of W: x-exponent from p down to 2
-        std::vector<int> fs, fd1, fd2;
+        // fold of W (x-exponent from p down to 2: W[m-2x+2y] -= W[m], W[m-2x+2z] -= W[m]),
+        // carried out on sparse linear combinations of the original components
+        std::vector<std::vector<std::pair<int, double>>> comb(f->np);
+        for (int i = 0; i < f->np; ++i) comb[i] = {{i, 1.0}};
+        auto axpy = [](std::vector<std::pair<int, double>> &dst, const std::vector<std::pair<int, double>> &src,
+                       double a) {
+            for (const auto &e : src) {
+                bool found = false;
+                for (auto &d : dst)
+                    if (d.first == e.first) { d.second += a * e.second; found = true; break; }
+                if (!found) dst.push_back({e.first, a * e.second});
+            }
+        };
         for (int a = order; a >= 2; --a)
             for (int i = 0; i < f->np; ++i)
                 if (mp.a[i] == a) {
-                    fs.push_back(i);
-                    fd1.push_back(mp.at(a - 2, mp.b[i] + 2, mp.c[i]));
-                    fd2.push_back(mp.at(a - 2, mp.b[i], mp.c[i] + 2));
+                    axpy(comb[mp.at(a - 2, mp.b[i] + 2, mp.c[i])], comb[i], -1.0);
+                    axpy(comb[mp.at(a - 2, mp.b[i], mp.c[i] + 2)], comb[i], -1.0);
+                    comb[i].clear();
                 }
-        f->nfold = (int)fs.size();
-        std::vector<int> fold;
-        fold.insert(fold.end(), fs.begin(), fs.end());
-        fold.insert(fold.end(), fd1.begin(), fd1.end());
-        fold.insert(fold.end(), fd2.begin(), fd2.end());
-        // completion of T: x-exponent from 2 up to p
-        std::vector<int> rk, rs1, rs2;
+        std::vector<int> fptr(1, 0), fcol;
+        std::vector<double> fval;
+        for (int r = 0; r < f->nr; ++r) {
+            auto row = comb[red[r]];
+            std::sort(row.begin(), row.end());
+            for (const auto &e : row)
+                if (e.second != 0.0) { fcol.push_back(e.first); fval.push_back(e.second); }
+            fptr.push_back((int)fcol.size());
+        }
+        // completion of T (x-exponent from 2 up: T[k] = -T[k-2x+2y] - T[k-2x+2z], plus
+        // the background on (2,0,0)), as combinations of the reduced T and the background
+        std::vector<std::vector<std::pair<int, double>>> tcomb(f->np);
+        std::vector<double> gbg(f->np, 0.0);
+        for (int r = 0; r < f->nr; ++r) tcomb[red[r]] = {{r, 1.0}};
         for (int a = 2; a <= order; ++a)
             for (int i = 0; i < f->np; ++i)
                 if (mp.a[i] == a) {
-                    rk.push_back(i);
-                    rs1.push_back(mp.at(a - 2, mp.b[i] + 2, mp.c[i]));
-                    rs2.push_back(mp.at(a - 2, mp.b[i], mp.c[i] + 2));
+                    const int s1 = mp.at(a - 2, mp.b[i] + 2, mp.c[i]), s2 = mp.at(a - 2, mp.b[i], mp.c[i] + 2);
+                    tcomb[i].clear();
+                    axpy(tcomb[i], tcomb[s1], -1.0);
+                    axpy(tcomb[i], tcomb[s2], -1.0);
+                    gbg[i] = -gbg[s1] - gbg[s2] + (a == 2 && mp.b[i] == 0 && mp.c[i] == 0 ? 1.0 : 0.0);
                 }
-        f->nrec = (int)rk.size();
-        f->k200 = order >= 2 ? mp.at(2, 0, 0) : -1;
-        std::vector<int> recon;
-        recon.insert(recon.end(), rk.begin(), rk.end());
-        recon.insert(recon.end(), rs1.begin(), rs1.end());
-        recon.insert(recon.end(), rs2.begin(), rs2.end());
+        std::vector<int> gptr(1, 0), gcol;
+        std::vector<double> gval;
+        for (int k = 0; k < f->np; ++k) {
+            auto row = tcomb[k];
+            std::sort(row.begin(), row.end());
+            for (const auto &e : row)
+                if (e.second != 0.0) { gcol.push_back(e.first); gval.push_back(e.second); }
+            gptr.push_back((int)gcol.size());
+        }
         for (int k = 0; k < f->nr; ++k)
             for (int m = 0; m < f->nr; ++m) {
                 const int ik = red[k], im = red[m];
@@ -553,23 +572,10 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
         for (int i = 0; i < f->nd; ++i) {
             dabc[i] = mq.a[stored[i]]; dabc[f->nd + i] = mq.b[stored[i]]; dabc[2 * f->nd + i] = mq.c[stored[i]];
         }
-        // Taylor gradient: every j with |j| <= p - 1
-        std::vector<int> ja, jb, jc, jp;
-        for (int i = 0; i < f->np; ++i) {
-            if (mp.a[i] + mp.b[i] + mp.c[i] > order - 1) continue;
-            ja.push_back(mp.a[i]); jb.push_back(mp.b[i]); jc.push_back(mp.c[i]);
-            jp.push_back(mp.at(mp.a[i] + 1, mp.b[i], mp.c[i]) | (mp.at(mp.a[i], mp.b[i] + 1, mp.c[i]) << 10) |
-                         (mp.at(mp.a[i], mp.b[i], mp.c[i] + 1) << 20));
-        }
-        f->ntay = (int)ja.size();
-        std::vector<int> tay;
-        tay.insert(tay.end(), ja.begin(), ja.end());
-        tay.insert(tay.end(), jb.begin(), jb.end());
-        tay.insert(tay.end(), jc.begin(), jc.end());
-        tay.insert(tay.end(), jp.begin(), jp.end());
-        if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->coef, coef)) || (e = upload(&f->fold, fold)) ||
-            (e = upload(&f->red, red)) || (e = upload(&f->conv_add, add)) || (e = upload(&f->recon, recon)) ||
-            (e = upload(&f->tay, tay)))
+        if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->coef, coef)) || (e = upload(&f->fptr, fptr)) ||
+            (e = upload(&f->fcol, fcol)) || (e = upload(&f->fval, fval)) || (e = upload(&f->gptr, gptr)) ||
+            (e = upload(&f->gcol, gcol)) || (e = upload(&f->gval, gval)) || (e = upload(&f->gbg, gbg)) ||
+            (e = upload(&f->conv_add, add)))
             return cuda_err(e, "tables");
         int *da = nullptr;
         if ((e = upload(&da, dabc))) return cuda_err(e, "tables");
@@ -644,11 +650,12 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
 cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
     FarState *f = c->far;
     const BoxDev &B = c->boxes_h[0];
-    k_far_multipoles<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->coef, f->fold, f->nfold, f->red, f->nr, f->W);
-    c->launches += 1;
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaEventRecord(c->ev_far[0], s);
     if (e) return e;
+    k_far_multipoles<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->coef, f->fptr, f->fcol, f->fval, f->nr, f->W);
+    c->launches += 1;
+    if ((e = cudaGetLastError())) return e;
     if (cufftSetStream(f->r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(f->r2c, f->W, f->Wh) != CUFFT_SUCCESS)
         return cudaErrorUnknown;
     // W_0 is reduced component 0: its zero-frequency value is the total mass,
@@ -658,17 +665,33 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
     const size_t smem = sizeof(double2) * 32 * (size_t)f->nr;
     e = cudaFuncSetAttribute(k_far_convolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
+    if ((e = cudaEventRecord(c->ev_far[2], s))) return e;
     k_far_convolve<<<grid_blocks(f->nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
         f->Dh, f->Wh, f->Th, f->nfreq, f->nr, f->conv_add);
     c->launches += 1;
     if ((e = cudaGetLastError())) return e;
+    if ((e = cudaEventRecord(c->ev_far[3], s))) return e;
     if (cufftSetStream(f->c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(f->c2r, f->Th, f->W) != CUFFT_SUCCESS)
         return cudaErrorUnknown;
-    k_far_taylor<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, c->perm, f->W, f->ncell, f->p, f->np, f->red, f->nr, f->recon, f->nrec,
-        f->k200, f->Wh, f->tay, f->ntay, 1.0 / (double)f->ncell, B.inv_h2_d, acc, accumulate);
+    void (*taylor)(const float4 *, const int *, const int *, const double *, int64_t, int, int, const int *,
+                   const int *, const double *, const double *, const cufftDoubleComplex *, double, double,
+                   float *, int) = nullptr;
+    switch (f->p) {
+        case 1: taylor = k_far_taylor<1>; break;
+        case 2: taylor = k_far_taylor<2>; break;
+        case 3: taylor = k_far_taylor<3>; break;
+        case 4: taylor = k_far_taylor<4>; break;
+        case 5: taylor = k_far_taylor<5>; break;
+        case 6: taylor = k_far_taylor<6>; break;
+        case 7: taylor = k_far_taylor<7>; break;
+        default: taylor = k_far_taylor<8>; break;
+    }
+    taylor<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+        c->sorted, c->cell_start, c->perm, f->W, f->ncell, f->np, f->nr, f->gptr, f->gcol, f->gval, f->gbg,
+        f->Wh, 1.0 / (double)f->ncell, B.inv_h2_d, acc, accumulate);
     c->launches += 1;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError())) return e;
+    return cudaEventRecord(c->ev_far[1], s);
 }
 
 }  // namespace nf

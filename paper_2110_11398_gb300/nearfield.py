@@ -299,7 +299,8 @@ class NearField:
         return {"n_particles": s.n_particles, "n_cells": s.n_cells, "interactions": s.interactions,
                 "max_occupancy": s.max_occupancy, "n_items": s.n_items,
                 "momentum": list(s.momentum), "abs_momentum": s.abs_momentum,
-                "bin_ms": s.bin_ms, "pair_ms": s.pair_ms, "kernel_launches": s.kernel_launches}
+                "bin_ms": s.bin_ms, "pair_ms": s.pair_ms, "kernel_launches": s.kernel_launches,
+                "far_ms": s.far_ms, "far_conv_ms": s.far_conv_ms}
 
     @property
     def tuning(self) -> dict:

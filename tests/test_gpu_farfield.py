@@ -89,6 +89,8 @@ def test_far_accumulates_onto_the_near_field(dev):
     far = nf.far()
     both = nf.far(out=near.clone(), accumulate=True)
     assert torch.equal(both, near + far)
+    st = nf.stats()
+    assert st["far_ms"] > 0 and 0 < st["far_conv_ms"] <= st["far_ms"]
     nf.close()
 
 
