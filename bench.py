@@ -53,8 +53,8 @@ def dist_env():
 # dram__bytes_write.sum) from one ncu capture each, with the sha256 of the
 # kernel source they were taken on; a changed source reports null.
 TRAFFIC_CAPTURES = {
-    ("early_256c_cpd65", "k_pairs"): (5.26e9 + 0.26691e9, "1adb8354156458dd336c04bab81f00b57e12ead3c4496e5abd2c90d42e8da52a"),
-    ("late_512c_cpd129", "k_pairs"): (57.17e9 + 2.67e9, "1adb8354156458dd336c04bab81f00b57e12ead3c4496e5abd2c90d42e8da52a"),
+    ("early_256c_cpd65", "k_pairs"): (5.53e9 + 0.26632e9, "e96ebc8e6f61f7ff6680e16752189133456437af99928bf685cb7388065468f3"),
+    ("late_512c_cpd129", "k_pairs"): (55.75e9 + 2.65e9, "e96ebc8e6f61f7ff6680e16752189133456437af99928bf685cb7388065468f3"),
 }
 
 
