@@ -124,3 +124,14 @@ def test_far_argument_errors(dev):
     with pytest.raises(NFError, match="NF_EINVAL"):
         nb.far_init(4)
     nb.close()
+
+
+@pytest.mark.parametrize("cpd,R", [(5, 1), (8, 3)])
+def test_far_matches_the_oracle_other_radii(dev, cpd, R):
+    rng = np.random.default_rng(20 + R)
+    n, L = 1500, 1.0
+    pos = rng.random((n, 3)).astype(np.float32)
+    got, _ = far_gpu(pos, L, cpd, 1e-3, dev, p=6, gm=1.0 / n, R=R)
+    ref = oracle.far_accel(pos.astype(np.float64), L, cpd, R, 6, m0=1.0 / n)
+    e = rel(got, ref)
+    assert np.median(e) < 2e-6 and np.quantile(e, 0.999) < 1e-4, (np.median(e), np.quantile(e, 0.999))

@@ -157,3 +157,19 @@ def test_far_field_follows_a_whole_cell_shift():
     shifted = np.mod(pos + np.array([2, 5, 1]) / cpd, L)
     far2 = oracle.far_accel(shifted, L, cpd, R, 6, mass=mass)
     assert np.abs(far2 - far).max() <= 1e-9 * np.abs(far).max()
+
+
+@pytest.mark.parametrize("cpd,R", [(5, 1), (8, 3)])
+def test_far_plus_near_equals_ewald_other_radii(cpd, R):
+    """The near-field radius moves images between the two parts; their sum
+    is the Ewald force whatever R is."""
+    pos, mass = _box(11 + R, 200)
+    L = 1.0
+    cid = oracle.bin_particles(pos.astype(np.float32), L, cpd)["cid"]
+    tot = oracle.ewald_accel(pos, L, mass=mass)
+    near = oracle.accel(pos, L, cpd, R, 1e-12, mass=mass, cid=cid)
+    far = oracle.far_accel(pos, L, cpd, R, 8, mass=mass, cid=cid)
+    e = np.linalg.norm(far + near - tot, axis=1) / np.linalg.norm(tot, axis=1)
+    # the error falls with the separation of the nearest far cells, R + 1:
+    # about 3e-5 at R = 1 and 4e-8 at R = 3 (p = 8)
+    assert np.median(e) < (1e-4 if R == 1 else 2e-7), np.median(e)
