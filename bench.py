@@ -356,6 +356,8 @@ class PlainRunner:
             self.vel = torch.from_numpy(v * np.float32(spacing)).to(dev)
             self.nf.bin(self.pos, gm=box.gm)
             self.nf.accel(out=self.out)
+            if self.far_order:   # the step then kicks with near + far
+                self.nf.far(out=self.out, accumulate=True)
             self.dt = self.nf.timestep(self.vel, self.out, 0.25)
 
     def step(self):
@@ -386,7 +388,8 @@ class PlainRunner:
             cfg["dt"] = self.dt
         if self.far_order:
             cfg["far_order"] = self.far_order
-            cfg["step"] = "bin, near-field accelerations, far-field accelerations (order %d)" % self.far_order
+            cfg["step"] = ("kick-drift-kick with near + far field (order %d)" % self.far_order if self.kdk else
+                           "bin, near-field accelerations, far-field accelerations (order %d)" % self.far_order)
         return cfg
 
     e2e_note = "nf_accel_host: H2D positions, bin, accelerations, D2H"
@@ -461,6 +464,12 @@ class PlainRunner:
             # the particles have moved: check the accelerations of the current positions
             cur = self.pos.cpu().numpy()
             self.box = synth_box_like(self.box, cur)
+            if self.far_order:
+                # the step's acc holds near + far and the end-to-end run has
+                # since re-binned other positions: re-bin these and take the
+                # near field alone, which the oracle sample checks
+                self.nf.bin(self.pos, gm=self.box.gm)
+                self.nf.accel(out=self.out)
         if self.law != "plummer" or self.kde_b:
             import oracle
             idx = np.sort(np.random.default_rng(5).choice(self.n, 4000, replace=False))

@@ -249,9 +249,11 @@ NF_API int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream)
  *             does). Cells are those of the last binning. Synchronises.
  * nf_kdk_step -- one step: v += a dt/2; x += v dt; re-bin x (same masses and
  *             box offsets as nf_bin_particles); a = near-field accelerations
- *             at the new x; v += a dt/2. On entry acc must hold the
- *             accelerations of the binned positions; on exit it holds those
- *             of the new positions. Synchronises (through the re-binning).
+ *             at the new x, plus the far field when nf_far_init has enabled
+ *             it (the total force); v += a dt/2. On entry acc must hold the
+ *             accelerations of the binned positions (near + far likewise);
+ *             on exit it holds those of the new positions. Synchronises
+ *             (through the re-binning).
  * Return NF_OK, NF_EINVAL, NF_ESTATE, NF_ERANGE (re-binning) or NF_ECUDA.
  */
 NF_API int nf_kick(nf_ctx *ctx, float *vel, const float *acc, double dt, void *stream);

@@ -234,16 +234,22 @@ def wrap_f32(x, L: float):
 
 
 def kdk_step(pos32, vel32, dt: float, L: float, cpd: int, R: int, eps: float, *, m0: float,
-             acc0=None):
+             acc0=None, far_order: int = 0):
     """One second-order kick-drift-kick leapfrog step with a global timestep
     (Sec. 2.4): v += a(x) dt/2; x += v dt (wrapped); v += a(x') dt/2, with the
-    near-field accelerations re-binned at x'. Positions and velocities are
-    float32 as on the device; the arithmetic is double. Returns
+    near-field accelerations re-binned at x' (plus the far field of order
+    ``far_order`` when it is > 0: the total force). Positions and velocities
+    are float32 as on the device; the arithmetic is double. Returns
     (pos, vel, acc at the new positions)."""
-    a0 = accel(pos32, L, cpd, R, eps, m0=m0) if acc0 is None else np.asarray(acc0, np.float64)
+    def total(x):
+        a = accel(x, L, cpd, R, eps, m0=m0)
+        if far_order:
+            a = a + far_accel(np.asarray(x, np.float64), L, cpd, R, far_order, m0=m0)
+        return a
+    a0 = total(pos32) if acc0 is None else np.asarray(acc0, np.float64)
     v_half = (np.asarray(vel32, np.float64) + 0.5 * dt * a0).astype(np.float32)
     x1 = wrap_f32(np.asarray(pos32, np.float64) + dt * v_half.astype(np.float64), L)
-    a1 = accel(x1, L, cpd, R, eps, m0=m0)
+    a1 = total(x1)
     v1 = (v_half.astype(np.float64) + 0.5 * dt * a1).astype(np.float32)
     return x1, v1, a1
 

@@ -608,6 +608,7 @@ int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const float *ma
     if ((rc = nf_drift(ctx, pos, vel, dt, stream))) return rc;
     if ((rc = nf_bin_particles(ctx, pos, mass, mass_if_null, n, box_offsets, stream))) return rc;
     if ((rc = nf_compute_accel(ctx, acc, stream))) return rc;
+    if (c->far && (rc = nf_compute_far(ctx, acc, 1, stream))) return rc;   // total force
     return nf_kick(ctx, vel, acc, 0.5 * dt, stream);
 }
 

@@ -109,3 +109,31 @@ def test_two_body_orbit_energy_on_gpu(dev):
         worst = max(worst, abs(energy() / e0 - 1))
     nf.close()
     assert worst < 3e-3, worst
+
+
+def test_kdk_steps_with_the_far_field(dev):
+    """With the far field enabled the step kicks with the total force."""
+    from paper_2110_11398_gb300 import NearField
+    box = synth.tiny(seed=8)
+    vel0 = (np.random.default_rng(3).standard_normal((box.n, 3)) * 0.05).astype(np.float32)
+    nf = NearField(box.L, box.cpd, box.eps, radius=box.R, capacity=box.n, device=dev)
+    nf.far_init(4)
+    pos = torch.from_numpy(box.pos.copy()).to(dev)
+    vel = torch.from_numpy(vel0.copy()).to(dev)
+    nf.bin(pos, gm=box.gm)
+    acc = nf.far(out=nf.accel(), accumulate=True)
+    dt = nf.timestep(vel, acc, 0.25)
+    x_ref, v_ref, a_ref = box.pos.copy(), vel0.copy(), None
+    for _ in range(2):
+        nf.kdk_step(pos, vel, acc, dt, gm=box.gm)
+        x_ref, v_ref, a_ref = oracle.kdk_step(x_ref, v_ref, dt, box.L, box.cpd, box.R, box.eps,
+                                              m0=box.gm, acc0=a_ref, far_order=4)
+    xg, vg, ag = pos.cpu().numpy(), vel.cpu().numpy(), acc.cpu().numpy()
+    D = (xg.astype(np.float64) - x_ref) - box.L * np.round((xg.astype(np.float64) - x_ref) / box.L)
+    assert np.abs(D).max() < 1e-6
+    ea = np.linalg.norm(ag.astype(np.float64) - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+    assert np.median(ea) < 1e-6, np.median(ea)
+    dv = np.linalg.norm(vg.astype(np.float64) - v_ref, axis=1)
+    kick = np.linalg.norm(v_ref.astype(np.float64) - vel0, axis=1)
+    assert np.median(dv / kick) < 1e-5, np.median(dv / kick)
+    nf.close()
