@@ -408,6 +408,10 @@ class PlainRunner:
             self.nf.accel_host(hpos, gm=self.box.gm, out=hacc)
         return (time.perf_counter() - t0) / reps, int(hpos.nbytes), int(hacc.nbytes)
 
+    def far_frequencies(self):
+        P = self.box.cpd
+        return P * P * (P // 2 + 1)
+
     def _e2e_far(self, reps):
         """Near + far field on host buffers: positions in, the total
         acceleration (near + far, summed on the device) back, every step."""
@@ -609,11 +613,25 @@ class BatchedRunner:
         self.passes = 1
         self.n_boxes_total = len(allb)
         self.gms = [b.gm for b in self.boxes]
+        self.far_order = getattr(args, "far", 0) or 0
+        self.far_init_s = None
+        if self.far_order:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            self.nf.far_init(self.far_order)
+            torch.cuda.synchronize()
+            self.far_init_s = time.perf_counter() - t0
+            self.far_out = torch.empty_like(self.out)
 
     def step(self):
         # equal masses within each box: per-box G m keeps the equal-mass kernel
         self.nf.bin(self.pos, gm=self.gms, box_offsets=self.offs)
         self.nf.accel(out=self.out)
+        if self.far_order:
+            self.nf.far(out=self.far_out)
+
+    def far_frequencies(self):
+        return sum(b.cpd * b.cpd * (b.cpd // 2 + 1) for b in self.boxes)
 
     def sequential_step(self):
         for nf, b, o0, o1 in zip(self.singles, self.boxes, self.offs[:-1], self.offs[1:]):
@@ -624,12 +642,35 @@ class BatchedRunner:
         return self.nf.stats()
 
     def config(self):
-        return {"workload": self.name, "n": self.n, "boxes": len(self.boxes),
-                "n_per_box": [int(b.n) for b in self.boxes][:64],
-                "cpd_per_box": [int(b.cpd) for b in self.boxes][:64], "R": 2}
+        cfg = {"workload": self.name, "n": self.n, "boxes": len(self.boxes),
+               "n_per_box": [int(b.n) for b in self.boxes][:64],
+               "cpd_per_box": [int(b.cpd) for b in self.boxes][:64], "R": 2}
+        if self.far_order:
+            cfg["far_order"] = self.far_order
+        return cfg
 
     def e2e(self, reps):
         torch = self.torch
+        if self.far_order:
+            # near + far on host buffers: positions in, total acceleration back
+            self.e2e_note = "H2D positions, bin, near field, far field added on, D2H total acceleration"
+            hp = self.pos.cpu().pin_memory()
+            ha = torch.empty((self.n, 3), dtype=torch.float32).pin_memory()
+            pos = torch.empty_like(self.pos)
+
+            def once():
+                pos.copy_(hp, non_blocking=True)
+                self.nf.bin(pos, gm=self.gms, box_offsets=self.offs)
+                self.nf.accel(out=self.out)
+                self.nf.far(out=self.out, accumulate=True)
+                ha.copy_(self.out, non_blocking=True)
+                torch.cuda.synchronize()
+
+            once()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                once()
+            return (time.perf_counter() - t0) / reps, int(hp.nbytes), int(ha.nbytes)
         hpos = self.pos.cpu().pin_memory().numpy()
         hacc = torch.empty((self.n, 3), dtype=torch.float32).pin_memory().numpy()
         self.nf.accel_host(hpos, gm=self.gms, out=hacc, box_offsets=self.offs)
@@ -759,8 +800,8 @@ def run_ours(args):
     roof_bin["frac"] = roof_bin["achieved"] / roof_bin["peak"]
     extra = {}
     if getattr(run, "far_order", 0):
-        P, p = run.box.cpd, run.far_order
-        nfreq = P * P * (P // 2 + 1)
+        p = run.far_order
+        nfreq = run.far_frequencies()
         nr = (p + 1) ** 2                      # reduced multipoles / Taylor coefficients
         conv_flops = 8.0 * nfreq * nr * nr     # complex FP64 multiply-add per (k, m, frequency)
         conv_ms = float(np.mean(far_conv_ms))

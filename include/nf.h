@@ -201,12 +201,13 @@ NF_API int nf_compute_accel_density(nf_ctx *ctx, float *acc, float *density, con
 NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *stream);
 
 /*
- * nf_far_init -- enables the far field of the near/far split for a one-box
- * context (Sec. 3.1: Taylor series of order p about every cell centre, their
+ * nf_far_init -- enables the far field of the near/far split (Sec. 3.1:
+ * Taylor series of order p about every cell centre, their
  * coefficients the cyclic convolution, done in Fourier space, of the cells'
  * multipole moments with the derivatives tensor of the periodic Green's
- * function). Builds that tensor once, for the context's CPD and near-field
- * radius R, with every image in the near field left out:
+ * function). Builds that tensor once per distinct CPD of the context's boxes
+ * (each box is its own periodic volume), for the near-field radius R, with
+ * every image in the near field left out:
  *     D_q(d) = sum_n d^q (1/r) at d + n CPD, d + n CPD not in [-R, R]^3,
  * |q| <= 2p, as an Ewald sum with a uniform background (forces from density
  * fluctuations, the periodic convention of cosmological codes).
@@ -214,8 +215,8 @@ NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, vo
  * Allocates about 16 (p + 1)(p + 2)(p + 3)(2p + 1)(2p + 2)(2p + 3) / 36 CPD^3
  * bytes for the transformed tensor (17 GB at p = 8, CPD = 129) plus as much
  * again while it is built. Synchronous.
- * Returns NF_OK, NF_EINVAL (order, CPD > 192, several boxes), NF_ENOMEM or
- * NF_ECUDA (cuFFT errors included).
+ * Returns NF_OK, NF_EINVAL (order, a CPD above 192), NF_ENOMEM or NF_ECUDA
+ * (cuFFT errors included).
  */
 NF_API int nf_far_init(nf_ctx *ctx, int order, void *stream);
 

@@ -524,9 +524,9 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
 int nf_far_init(nf_ctx *ctx, int order, void *stream) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, NF_EINVAL, "nf_far_init: ctx is NULL");
-    if (c->n_boxes != 1) return fail(c, NF_EINVAL, "nf_far_init: the far field needs a one-box context");
     if (order < 1 || order > 8) return fail(c, NF_EINVAL, "nf_far_init: order must be in [1, 8]");
-    if (c->boxes_h[0].cpd > 192) return fail(c, NF_EINVAL, "nf_far_init: CPD above 192 is not supported");
+    for (const nf::BoxDev &B : c->boxes_h)
+        if (B.cpd > 192) return fail(c, NF_EINVAL, "nf_far_init: CPD above 192 is not supported");
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     std::string err;

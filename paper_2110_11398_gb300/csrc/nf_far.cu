@@ -64,14 +64,28 @@ struct MultiIndex {
     int at(int aa, int bb, int cc) const { return pos[((size_t)aa * (n + 1) + bb) * (n + 1) + cc]; }
 };
 
-struct FarState {
-    int p = 0, P = 0, np = 0, nr = 0, nd = 0;
-    double alpha = 0.0;
+// Derivatives tensor of one CPD (boxes of equal CPD share it) and the
+// batched transform plans of that size.
+struct FarTensor {
+    int P = 0;
     int64_t ncell = 0, nfreq = 0;
+    cufftDoubleComplex *Dh = nullptr;  // [nd][nfreq] tensor, x-exponent <= 2
+    cufftHandle r2c = 0, c2r = 0;      // nr components at a time
+    bool r2c_ok = false, c2r_ok = false;
+};
+
+// Per-box buffers of a step.
+struct FarBox {
+    int tensor = 0;
+    int64_t cell0 = 0;                 // first global cell of the box
+    double inv_h2 = 0.0;
     double *W = nullptr;               // [nr][ncell] reduced weighted multipoles, then the reduced T
     cufftDoubleComplex *Wh = nullptr;  // [nr][nfreq]
     cufftDoubleComplex *Th = nullptr;  // [nr][nfreq]
-    cufftDoubleComplex *Dh = nullptr;  // [nd][nfreq] tensor, x-exponent <= 2
+};
+
+struct FarState {
+    int p = 0, np = 0, nr = 0, nd = 0;
     int *mabc = nullptr;               // [3][np] all multi-indices of order <= p
     double *coef = nullptr;            // [np] (-1)^|m| / m!
     // fold: reduced W_r = sum_e fval[e] * (coef M)[fcol[e]], e in [fptr[r], fptr[r+1])
@@ -81,8 +95,8 @@ struct FarState {
     int *gptr = nullptr, *gcol = nullptr;
     double *gval = nullptr, *gbg = nullptr;
     int *conv_add = nullptr;           // [nr][nr] position of k + m among the stored tensor components
-    cufftHandle r2c = 0, c2r = 0;
-    bool r2c_ok = false, c2r_ok = false;
+    std::vector<FarTensor> tensors;
+    std::vector<FarBox> boxes;
 };
 
 namespace {
@@ -448,38 +462,36 @@ int grid_blocks(int64_t n, int threads, int sm_count, int per_sm) {
 void far_release(Ctx *c) {
     FarState *f = c->far;
     if (!f) return;
-    void *bufs[] = {f->W, f->Wh, f->Th, f->Dh, f->mabc, f->coef, f->fptr, f->fcol, f->fval,
-                    f->gptr, f->gcol, f->gval, f->gbg, f->conv_add};
+    void *bufs[] = {f->mabc, f->coef, f->fptr, f->fcol, f->fval, f->gptr, f->gcol, f->gval, f->gbg,
+                    f->conv_add};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    if (f->r2c_ok) cufftDestroy(f->r2c);
-    if (f->c2r_ok) cufftDestroy(f->c2r);
+    for (FarTensor &t : f->tensors) {
+        if (t.Dh) cudaFree(t.Dh);
+        if (t.r2c_ok) cufftDestroy(t.r2c);
+        if (t.c2r_ok) cufftDestroy(t.c2r);
+    }
+    for (FarBox &b : f->boxes) {
+        void *bb[] = {b.W, b.Wh, b.Th};
+        for (void *x : bb)
+            if (x) cudaFree(x);
+    }
     delete f;
     c->far = nullptr;
 }
 
-// Builds the far-field state of a one-box context: index tables, the
-// derivatives tensor in Fourier space, buffers and FFT plans. Synchronous.
-// Returns NF_OK, or NF_ENOMEM / NF_ECUDA with `err` set.
+// Builds the far-field state: index tables (one set for the order), one
+// derivatives tensor in Fourier space per distinct CPD, per-box buffers and
+// FFT plans. Synchronous. Returns NF_OK, or NF_ENOMEM / NF_ECUDA with `err` set.
 int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
     far_release(c);
     FarState *f = new FarState();
     c->far = f;
-    const BoxDev &B = c->boxes_h[0];
     f->p = order;
-    f->P = B.cpd;
-    const int P = f->P;
-    f->ncell = (int64_t)P * P * P;
-    f->nfreq = (int64_t)P * P * (P / 2 + 1);
     MultiIndex mp, mq;
     mp.build(order);
     mq.build(2 * order);
     f->np = mp.size();
-    // splitting: the real-space part reaches r < (6.5 + q/4)/alpha cells and the
-    // Fourier part |k| < (13 + q/2) alpha; alpha = max(0.5, 3.5/P) keeps both small
-    f->alpha = std::max(0.5, 3.5 / P);
-    const double r_cut = (6.5 + 0.25 * mq.n) / f->alpha;
-    const double k_cut = (13.0 + 0.5 * mq.n) * f->alpha;
     auto cuda_err = [&](cudaError_t e, const char *what) {
         err = std::string("nf_far_init: ") + what + ": " + cudaGetErrorString(e);
         far_release(c);
@@ -577,102 +589,138 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             (e = upload(&f->gcol, gcol)) || (e = upload(&f->gval, gval)) || (e = upload(&f->gbg, gbg)) ||
             (e = upload(&f->conv_add, add)))
             return cuda_err(e, "tables");
-        int *da = nullptr;
-        if ((e = upload(&da, dabc))) return cuda_err(e, "tables");
-        // ---- real-space part of the tensor (host), scattered into a zeroed FP64 grid
-        std::vector<int64_t> cells;
-        std::vector<double> vals;
-        real_space_part(P, c->R, f->alpha, r_cut, mq, stored, cells, vals);
-        double *grid = nullptr, *dvals = nullptr;
-        int64_t *dcells = nullptr;
-        if ((e = dmalloc(&f->Dh, (size_t)f->nd * f->nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
-        if ((e = dmalloc(&grid, (size_t)f->nd * f->ncell)) || (e = upload(&dvals, vals)) || (e = upload(&dcells, cells))) {
-            cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
-            return cuda_err(e, "tensor");
-        }
-        e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nd * f->ncell, s);
-        if (!e) {
-            k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nd, 256, c->sm_count, 8), 256, 0, s>>>(
-                dvals, dcells, (int64_t)cells.size(), f->nd, f->ncell, grid);
-            e = cudaGetLastError();
-        }
-        // the tensor's components are transformed 64 at a time, the rest by a
-        // second plan: chunk starts stay at even component offsets, which
-        // keeps them 16-byte aligned as cuFFT requires of its data
-        cufftHandle plan = 0, plan_rest = 0;
-        int dims[3] = {P, P, P};
-        const int chunk = 64, rest = f->nd % chunk;
-        const char *stage = "tensor transform: plan";
-        cufftResult fr = CUFFT_SUCCESS;
-        if (!e && f->nd >= chunk)
-            fr = cufftPlanMany(&plan, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, chunk);
-        if (!e && fr == CUFFT_SUCCESS && rest)
-            fr = cufftPlanMany(&plan_rest, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq, CUFFT_D2Z, rest);
-        if (!e && fr == CUFFT_SUCCESS) {
-            stage = "tensor transform: stream";
-            if (plan) fr = cufftSetStream(plan, s);
-            if (fr == CUFFT_SUCCESS && plan_rest) fr = cufftSetStream(plan_rest, s);
-        }
-        for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nd; q0 += chunk) {
-            stage = "tensor transform: exec";
-            fr = cufftExecD2Z(q0 + chunk <= f->nd ? plan : plan_rest, grid + (size_t)q0 * f->ncell,
-                              f->Dh + (size_t)q0 * f->nfreq);
-        }
-        if (!e && fr == CUFFT_SUCCESS) {
-            k_far_longrange<<<grid_blocks(f->nfreq, 128, c->sm_count, 8), 128, 0, s>>>(
-                f->Dh, P, f->nfreq, f->nd, da, da + f->nd, da + 2 * f->nd, f->alpha, k_cut);
-            e = cudaGetLastError();
-        }
-        if (!e) e = cudaStreamSynchronize(s);
-        if (plan) cufftDestroy(plan);
-        if (plan_rest) cufftDestroy(plan_rest);
-        cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
-        if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
-        if (e) return cuda_err(e, "tensor");
     }
-    // ---- per-step buffers and plans (reduced components)
-    if ((e = dmalloc(&f->W, (size_t)f->nr * f->ncell)) || (e = dmalloc(&f->Wh, (size_t)f->nr * f->nfreq)) ||
-        (e = dmalloc(&f->Th, (size_t)f->nr * f->nfreq)))
-        return cuda_err(e, "buffers");
-    int dims[3] = {P, P, P};
-    cufftResult fr = cufftPlanMany(&f->r2c, 3, dims, nullptr, 1, (int)f->ncell, nullptr, 1, (int)f->nfreq,
-                                   CUFFT_D2Z, f->nr);
-    if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
-    f->r2c_ok = true;
-    fr = cufftPlanMany(&f->c2r, 3, dims, nullptr, 1, (int)f->nfreq, nullptr, 1, (int)f->ncell, CUFFT_Z2D, f->nr);
-    if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
-    f->c2r_ok = true;
+    std::vector<int> dabc(3 * (size_t)f->nd);
+    for (int i = 0; i < f->nd; ++i) {
+        dabc[i] = mq.a[stored[i]]; dabc[f->nd + i] = mq.b[stored[i]]; dabc[2 * f->nd + i] = mq.c[stored[i]];
+    }
+    // ---- one tensor per distinct CPD
+    for (int b = 0; b < c->n_boxes; ++b) {
+        const BoxDev &B = c->boxes_h[b];
+        const int P = B.cpd;
+        int ti = -1;
+        for (size_t t = 0; t < f->tensors.size(); ++t)
+            if (f->tensors[t].P == P) ti = (int)t;
+        if (ti < 0) {
+            ti = (int)f->tensors.size();
+            f->tensors.emplace_back();
+            FarTensor &T = f->tensors.back();
+            T.P = P;
+            T.ncell = (int64_t)P * P * P;
+            T.nfreq = (int64_t)P * P * (P / 2 + 1);
+            // splitting: the real-space part reaches r < (6.5 + q/4)/alpha cells and the
+            // Fourier part |k| < (13 + q/2) alpha; alpha = max(0.5, 3.5/P) keeps both small
+            const double alpha = std::max(0.5, 3.5 / P);
+            const double r_cut = (6.5 + 0.25 * mq.n) / alpha;
+            const double k_cut = (13.0 + 0.5 * mq.n) * alpha;
+            int *da = nullptr;
+            if ((e = upload(&da, dabc))) return cuda_err(e, "tables");
+            // real-space part (host), scattered into a zeroed FP64 grid
+            std::vector<int64_t> cells;
+            std::vector<double> vals;
+            real_space_part(P, c->R, alpha, r_cut, mq, stored, cells, vals);
+            double *grid = nullptr, *dvals = nullptr;
+            int64_t *dcells = nullptr;
+            if ((e = dmalloc(&T.Dh, (size_t)f->nd * T.nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
+            if ((e = dmalloc(&grid, (size_t)f->nd * T.ncell)) || (e = upload(&dvals, vals)) ||
+                (e = upload(&dcells, cells))) {
+                cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+                return cuda_err(e, "tensor");
+            }
+            e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nd * T.ncell, s);
+            if (!e) {
+                k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nd, 256, c->sm_count, 8), 256, 0, s>>>(
+                    dvals, dcells, (int64_t)cells.size(), f->nd, T.ncell, grid);
+                e = cudaGetLastError();
+            }
+            // the tensor's components are transformed 64 at a time, the rest by a
+            // second plan: chunk starts stay at even component offsets, which
+            // keeps them 16-byte aligned as cuFFT requires of its data
+            cufftHandle plan = 0, plan_rest = 0;
+            int dims[3] = {P, P, P};
+            const int chunk = 64, rest = f->nd % chunk;
+            const char *stage = "tensor transform: plan";
+            cufftResult fr = CUFFT_SUCCESS;
+            if (!e && f->nd >= chunk)
+                fr = cufftPlanMany(&plan, 3, dims, nullptr, 1, (int)T.ncell, nullptr, 1, (int)T.nfreq, CUFFT_D2Z, chunk);
+            if (!e && fr == CUFFT_SUCCESS && rest)
+                fr = cufftPlanMany(&plan_rest, 3, dims, nullptr, 1, (int)T.ncell, nullptr, 1, (int)T.nfreq, CUFFT_D2Z,
+                                   rest);
+            if (!e && fr == CUFFT_SUCCESS) {
+                stage = "tensor transform: stream";
+                if (plan) fr = cufftSetStream(plan, s);
+                if (fr == CUFFT_SUCCESS && plan_rest) fr = cufftSetStream(plan_rest, s);
+            }
+            for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nd; q0 += chunk) {
+                stage = "tensor transform: exec";
+                fr = cufftExecD2Z(q0 + chunk <= f->nd ? plan : plan_rest, grid + (size_t)q0 * T.ncell,
+                                  T.Dh + (size_t)q0 * T.nfreq);
+            }
+            if (!e && fr == CUFFT_SUCCESS) {
+                k_far_longrange<<<grid_blocks(T.nfreq, 128, c->sm_count, 8), 128, 0, s>>>(
+                    T.Dh, P, T.nfreq, f->nd, da, da + f->nd, da + 2 * f->nd, alpha, k_cut);
+                e = cudaGetLastError();
+            }
+            if (!e) e = cudaStreamSynchronize(s);
+            if (plan) cufftDestroy(plan);
+            if (plan_rest) cufftDestroy(plan_rest);
+            cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+            if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
+            if (e) return cuda_err(e, "tensor");
+            // per-step plans of this size (reduced components)
+            fr = cufftPlanMany(&T.r2c, 3, dims, nullptr, 1, (int)T.ncell, nullptr, 1, (int)T.nfreq, CUFFT_D2Z, f->nr);
+            if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
+            T.r2c_ok = true;
+            fr = cufftPlanMany(&T.c2r, 3, dims, nullptr, 1, (int)T.nfreq, nullptr, 1, (int)T.ncell, CUFFT_Z2D, f->nr);
+            if (fr != CUFFT_SUCCESS) return fft_err(fr, "plan");
+            T.c2r_ok = true;
+        }
+        f->boxes.emplace_back();
+        FarBox &X = f->boxes.back();
+        X.tensor = ti;
+        X.cell0 = B.cell_off;
+        X.inv_h2 = B.inv_h2_d;
+        const FarTensor &T = f->tensors[ti];
+        if ((e = dmalloc(&X.W, (size_t)f->nr * T.ncell)) || (e = dmalloc(&X.Wh, (size_t)f->nr * T.nfreq)) ||
+            (e = dmalloc(&X.Th, (size_t)f->nr * T.nfreq)))
+            return cuda_err(e, "buffers");
+    }
     return NF_OK;
 }
 
 // Far-field accelerations of the binned particles, input order, written to
-// (or, with accumulate, added into) acc. Enqueued on s.
+// (or, with accumulate, added into) acc. Enqueued on s, phase by phase over
+// the boxes.
 cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
     FarState *f = c->far;
-    const BoxDev &B = c->boxes_h[0];
     cudaError_t e = cudaEventRecord(c->ev_far[0], s);
     if (e) return e;
-    k_far_multipoles<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, f->ncell, f->p, f->np, f->mabc, f->coef, f->fptr, f->fcol, f->fval, f->nr, f->W);
-    c->launches += 1;
-    if ((e = cudaGetLastError())) return e;
-    if (cufftSetStream(f->r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(f->r2c, f->W, f->Wh) != CUFFT_SUCCESS)
-        return cudaErrorUnknown;
-    // W_0 is reduced component 0: its zero-frequency value is the total mass,
-    // read by the Taylor kernel for the background term (the inverse
-    // transform below overwrites Th only)
+    for (const FarBox &X : f->boxes) {
+        const FarTensor &T = f->tensors[X.tensor];
+        k_far_multipoles<<<grid_blocks(T.ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+            c->sorted, c->cell_start + X.cell0, T.ncell, f->p, f->np, f->mabc, f->coef, f->fptr, f->fcol, f->fval,
+            f->nr, X.W);
+        c->launches += 1;
+        if ((e = cudaGetLastError())) return e;
+        if (cufftSetStream(T.r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(T.r2c, X.W, X.Wh) != CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+    }
+    // W_0 is reduced component 0: its zero-frequency value is the box's total
+    // mass, read by the Taylor kernel for the background term (the inverse
+    // transforms overwrite Th only)
     const int ny = 8;
     const size_t smem = sizeof(double2) * 32 * (size_t)f->nr;
     e = cudaFuncSetAttribute(k_far_convolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e) return e;
     if ((e = cudaEventRecord(c->ev_far[2], s))) return e;
-    k_far_convolve<<<grid_blocks(f->nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
-        f->Dh, f->Wh, f->Th, f->nfreq, f->nr, f->conv_add);
-    c->launches += 1;
-    if ((e = cudaGetLastError())) return e;
+    for (const FarBox &X : f->boxes) {
+        const FarTensor &T = f->tensors[X.tensor];
+        k_far_convolve<<<grid_blocks(T.nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
+            T.Dh, X.Wh, X.Th, T.nfreq, f->nr, f->conv_add);
+        c->launches += 1;
+        if ((e = cudaGetLastError())) return e;
+    }
     if ((e = cudaEventRecord(c->ev_far[3], s))) return e;
-    if (cufftSetStream(f->c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(f->c2r, f->Th, f->W) != CUFFT_SUCCESS)
-        return cudaErrorUnknown;
     void (*taylor)(const float4 *, const int *, const int *, const double *, int64_t, int, int, const int *,
                    const int *, const double *, const double *, const cufftDoubleComplex *, double, double,
                    float *, int) = nullptr;
@@ -686,11 +734,16 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
         case 7: taylor = k_far_taylor<7>; break;
         default: taylor = k_far_taylor<8>; break;
     }
-    taylor<<<grid_blocks(f->ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-        c->sorted, c->cell_start, c->perm, f->W, f->ncell, f->np, f->nr, f->gptr, f->gcol, f->gval, f->gbg,
-        f->Wh, 1.0 / (double)f->ncell, B.inv_h2_d, acc, accumulate);
-    c->launches += 1;
-    if ((e = cudaGetLastError())) return e;
+    for (const FarBox &X : f->boxes) {
+        const FarTensor &T = f->tensors[X.tensor];
+        if (cufftSetStream(T.c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(T.c2r, X.Th, X.W) != CUFFT_SUCCESS)
+            return cudaErrorUnknown;
+        taylor<<<grid_blocks(T.ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+            c->sorted, c->cell_start + X.cell0, c->perm, X.W, T.ncell, f->np, f->nr, f->gptr, f->gcol, f->gval,
+            f->gbg, X.Wh, 1.0 / (double)T.ncell, X.inv_h2, acc, accumulate);
+        c->launches += 1;
+        if ((e = cudaGetLastError())) return e;
+    }
     return cudaEventRecord(c->ev_far[1], s);
 }
 

@@ -188,8 +188,8 @@ class NearField:
 
     # ------------------------------------------------------------ far field
     def far_init(self, order: int = 8) -> None:
-        """Enable the far field of order ``order`` (one-box contexts): builds
-        the derivatives tensor for this CPD and near-field radius."""
+        """Enable the far field of order ``order``: builds the derivatives
+        tensor for each distinct CPD of the boxes and the near-field radius."""
         N.check(self._lib.nf_far_init(self._ctx, int(order), _stream_ptr(self.device)), self._ctx,
                 "nf_far_init")
 

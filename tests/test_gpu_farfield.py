@@ -120,10 +120,30 @@ def test_far_argument_errors(dev):
     with pytest.raises(NFError, match="NF_EINVAL"):
         nf.far_init(0)
     nf.close()
-    nb = NearField([1.0, 1.0], [5, 7], [1e-3, 1e-3], capacity=100, device=dev)
-    with pytest.raises(NFError, match="NF_EINVAL"):
-        nb.far_init(4)
+
+
+def test_batched_far_field_equals_each_box_alone(dev):
+    """Several boxes in one context (two share a CPD, so they share a tensor):
+    each box's far field equals that of its own one-box context bit for bit,
+    and the oracle's."""
+    from paper_2110_11398_gb300 import NearField
+    rng = np.random.default_rng(30)
+    specs = [(1.0, 7, 900), (2.0, 5, 600), (1.0, 7, 1200)]
+    pos = [(rng.random((n, 3)) * L).astype(np.float32) for L, _, n in specs]
+    offs = np.cumsum([0] + [n for _, _, n in specs])
+    gms = [1.0 / n for _, _, n in specs]
+    nb = NearField([L for L, _, _ in specs], [c for _, c, _ in specs], [1e-3] * 3, capacity=int(offs[-1]),
+                   device=dev)
+    nb.far_init(6)
+    nb.bin(torch.from_numpy(np.concatenate(pos)).to(dev), gm=gms, box_offsets=offs)
+    fb = nb.far().cpu().numpy()
     nb.close()
+    for (L, cpd, n), x, gm, o0, o1 in zip(specs, pos, gms, offs[:-1], offs[1:]):
+        got, _ = far_gpu(x, L, cpd, 1e-3, dev, p=6, gm=gm)
+        assert np.array_equal(fb[o0:o1].view(np.uint32), got.view(np.uint32))
+        ref = oracle.far_accel(x.astype(np.float64), L, cpd, 2, 6, m0=gm)
+        e = rel(got, ref)
+        assert np.median(e) < 2e-6, np.median(e)
 
 
 @pytest.mark.parametrize("cpd,R", [(5, 1), (8, 3)])
