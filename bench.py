@@ -719,6 +719,8 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     dist_or_none = dist if world > 1 else None
 
+    if args.far and args.workload == "adjoint":
+        raise SystemExit("--far goes with the force workloads (tiny, early, late, batched), not the adjoint")
     if args.workload == "batched":
         run = BatchedRunner(args, dev, rank, world)
         scaling = "strong"

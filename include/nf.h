@@ -212,9 +212,11 @@ NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, vo
  * |q| <= 2p, as an Ewald sum with a uniform background (forces from density
  * fluctuations, the periodic convention of cosmological codes).
  *   order   p in [1, 8] (the paper uses 8)
- * Allocates about 16 (p + 1)(p + 2)(p + 3)(2p + 1)(2p + 2)(2p + 3) / 36 CPD^3
- * bytes for the transformed tensor (17 GB at p = 8, CPD = 129) plus as much
- * again while it is built. Synchronous.
+ * Only the tensor components with x-exponent <= 2 are kept (the tensor is
+ * harmonic, which fixes the rest): 409 of them at p = 8, about
+ * 8 x 409 CPD^3 bytes in Fourier space (7 GB at CPD = 129), plus as much
+ * again while it is built, and 3 x 8 (p+1)^2 CPD^3 bytes of per-step
+ * buffers per box. Synchronous.
  * Returns NF_OK, NF_EINVAL (order, a CPD above 192), NF_ENOMEM or NF_ECUDA
  * (cuFFT errors included).
  */
@@ -230,7 +232,7 @@ NF_API int nf_far_init(nf_ctx *ctx, int order, void *stream);
  *   acc         device [N x 3] float32, input order; written, or with
  *               accumulate != 0 added to (e.g. onto the near field)
  * Returns NF_OK, NF_ESTATE (no nf_far_init or no binning), NF_EINVAL or
- * NF_ECUDA. Asynchronous.
+ * NF_ECUDA (a cuFFT failure included, named in nf_last_error). Asynchronous.
  */
 NF_API int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream);
 

@@ -546,7 +546,9 @@ int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream) {
     if (c->n == 0) return NF_OK;
     for (cudaEvent_t &ev : c->ev_far)
         if (!ev) NF_CK(c, cudaEventCreate(&ev));
-    cudaError_t e = far_compute(c, acc, accumulate ? 1 : 0, s);
+    std::string fft_fail;
+    cudaError_t e = far_compute(c, acc, accumulate ? 1 : 0, s, fft_fail);
+    if (!fft_fail.empty()) return fail(c, NF_ECUDA, "nf_compute_far: " + fft_fail);
     if (e) return cuda_fail(c, e, "nf_compute_far");
     c->have_far_time = 1;
     c->last_stream = s;

@@ -96,7 +96,7 @@ struct Ctx {
 
 // far field (nf_far.cu)
 int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err);
-cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s);
+cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s, std::string &fft_fail);
 void far_release(Ctx *c);
 
 constexpr int kMomBlocks = 512;

@@ -691,7 +691,7 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
 // Far-field accelerations of the binned particles, input order, written to
 // (or, with accumulate, added into) acc. Enqueued on s, phase by phase over
 // the boxes.
-cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
+cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s, std::string &fft_fail) {
     FarState *f = c->far;
     cudaError_t e = cudaEventRecord(c->ev_far[0], s);
     if (e) return e;
@@ -702,8 +702,12 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
             f->nr, X.W);
         c->launches += 1;
         if ((e = cudaGetLastError())) return e;
-        if (cufftSetStream(T.r2c, s) != CUFFT_SUCCESS || cufftExecD2Z(T.r2c, X.W, X.Wh) != CUFFT_SUCCESS)
+        cufftResult fr = cufftSetStream(T.r2c, s);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecD2Z(T.r2c, X.W, X.Wh);
+        if (fr != CUFFT_SUCCESS) {
+            fft_fail = "forward transform of the multipoles: cuFFT error " + std::to_string((int)fr);
             return cudaErrorUnknown;
+        }
     }
     // W_0 is reduced component 0: its zero-frequency value is the box's total
     // mass, read by the Taylor kernel for the background term (the inverse
@@ -736,8 +740,12 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s) {
     }
     for (const FarBox &X : f->boxes) {
         const FarTensor &T = f->tensors[X.tensor];
-        if (cufftSetStream(T.c2r, s) != CUFFT_SUCCESS || cufftExecZ2D(T.c2r, X.Th, X.W) != CUFFT_SUCCESS)
+        cufftResult fr = cufftSetStream(T.c2r, s);
+        if (fr == CUFFT_SUCCESS) fr = cufftExecZ2D(T.c2r, X.Th, X.W);
+        if (fr != CUFFT_SUCCESS) {
+            fft_fail = "inverse transform of the Taylor coefficients: cuFFT error " + std::to_string((int)fr);
             return cudaErrorUnknown;
+        }
         taylor<<<grid_blocks(T.ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
             c->sorted, c->cell_start + X.cell0, c->perm, X.W, T.ncell, f->np, f->nr, f->gptr, f->gcol, f->gval,
             f->gbg, X.Wh, 1.0 / (double)T.ncell, X.inv_h2, acc, accumulate);
