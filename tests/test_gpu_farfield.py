@@ -155,3 +155,34 @@ def test_far_matches_the_oracle_other_radii(dev, cpd, R):
     ref = oracle.far_accel(pos.astype(np.float64), L, cpd, R, 6, m0=1.0 / n)
     e = rel(got, ref)
     assert np.median(e) < 2e-6 and np.quantile(e, 0.999) < 1e-4, (np.median(e), np.quantile(e, 0.999))
+
+
+def test_far_field_properties_at_full_early_size(dev):
+    """The 16.8M-particle early box (CPD 65) at p = 8, in the configuration the
+    benchmark times, checked by properties that hold at any size: the far
+    momentum sum_i m a_i cancels (each pair's two far terms are opposite, up
+    to the truncation); a shift of every particle by whole cells moves the far
+    field with them; and p = 6 is within the truncation error of p = 8."""
+    from paper_2110_11398_gb300 import NearField
+    box = synth.early()
+    nf = NearField(box.L, box.cpd, box.eps, capacity=box.n, device=dev)
+    pos = torch.from_numpy(box.pos).to(dev)
+    nf.far_init(8)
+    nf.bin(pos, gm=box.gm)
+    a8 = nf.far()
+    mom = a8.double().sum(0).abs().max().item()
+    assert mom <= 1e-5 * a8.double().norm(dim=1).sum().item(), mom
+    # whole-cell shift (3, 5, 1) cells, wrapped; float32 shifts are exact here
+    # up to the rounding of x + k h, about 1e-7 cells
+    shift = torch.tensor([3.0, 5.0, 1.0], dtype=torch.float64, device=dev) * (box.L / box.cpd)
+    moved = torch.remainder(pos.double() + shift, box.L).float()
+    nf.bin(moved, gm=box.gm)
+    a8s = nf.far()
+    d = (a8s - a8).double().norm(dim=1) / a8.double().norm(dim=1)
+    assert d.median().item() < 1e-5, d.median().item()
+    nf.far_init(6)
+    nf.bin(pos, gm=box.gm)
+    a6 = nf.far()
+    d6 = (a6 - a8).double().norm(dim=1) / a8.double().norm(dim=1)
+    assert d6.median().item() < 1e-4, d6.median().item()
+    nf.close()
