@@ -100,6 +100,7 @@ typedef struct nf_tuning {
     int warps_per_block;
     int blocks_per_sm;
     int use_graph;
+    int vjp_sinks_per_lane;   /* sinks per lane of the adjoint kernel; 0 = as sinks_per_lane */
 } nf_tuning;
 
 /*

@@ -38,7 +38,8 @@ class nf_stats(ctypes.Structure):
 
 class nf_tuning(ctypes.Structure):
     _fields_ = [("sinks_per_lane", ctypes.c_int), ("warps_per_block", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("vjp_sinks_per_lane", ctypes.c_int)]
 
 
 class NFError(RuntimeError):

@@ -94,21 +94,33 @@ struct DeviceGuard {
 };
 
 bool valid_tuning(const nf_tuning &t) {
-    const int k = t.sinks_per_lane, w = t.warps_per_block;
+    const int k = t.sinks_per_lane, w = t.warps_per_block, kv = t.vjp_sinks_per_lane;
     return (k == 1 || k == 2 || k == 4) && (w == 2 || w == 4 || w == 8 || w == 16) &&
-           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32;
+           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32 && (kv == 0 || kv == 1 || kv == 2 || kv == 4);
 }
 
+int decomp_slot(int K) { return K == 1 ? 0 : (K == 2 ? 1 : 2); }
+
+// Selects the item decomposition for K sinks per lane. Each K has its own
+// table (uploaded once, synchronously, so that graphs captured afterwards
+// see it), so the forward and adjoint kernels can alternate without copies.
 int ensure_decomp(Ctx *c, int K, cudaStream_t s) {
-    if (c->decomp_k == K) return NF_OK;
-    nf::Decomp h;
-    nf::make_decomp(K, &h);
-    // the table is read by the work-list kernels; a synchronous copy keeps it
-    // valid for graphs captured afterwards
-    NF_CK(c, cudaStreamSynchronize(s));
-    NF_CK(c, cudaMemcpy(c->decomp_d, &h, sizeof(h), cudaMemcpyHostToDevice));
+    const int slot = decomp_slot(K);
+    if (!(c->decomp_built & (1 << slot))) {
+        nf::Decomp h;
+        nf::make_decomp(K, &h);
+        NF_CK(c, cudaStreamSynchronize(s));
+        NF_CK(c, cudaMemcpy(c->decomp_d + slot, &h, sizeof(h), cudaMemcpyHostToDevice));
+        c->decomp_built |= 1 << slot;
+    }
     c->decomp_k = K;
     return NF_OK;
+}
+
+// Sinks per lane of the adjoint kernel.
+int vjp_k(const Ctx *c) {
+    if (c->precision == NF_PREC_FP64_REF) return 1;
+    return c->tune.vjp_sinks_per_lane ? c->tune.vjp_sinks_per_lane : c->tune.sinks_per_lane;
 }
 
 // Event record that stays a real (timed) record when `s` is being captured
@@ -140,7 +152,9 @@ cudaError_t enqueue_vjp(Ctx *c, const float *w, float *grad, cudaStream_t s) {
     cudaError_t e;
     if ((e = nf::launch_worklist(c, s))) return e;
     if ((e = record_timing(c->ev_pair0, s))) return e;
-    if ((e = nf::launch_vjp(c, w, grad, c->tune, s))) return e;
+    nf_tuning t = c->tune;
+    t.sinks_per_lane = vjp_k(c);
+    if ((e = nf::launch_vjp(c, w, grad, t, s))) return e;
     if ((e = record_timing(c->ev_pair1, s))) return e;
     return cudaMemcpyAsync(c->state_h, c->state, sizeof(nf::DevState), cudaMemcpyDeviceToHost, s);
 }
@@ -333,7 +347,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     NF_AL(c->w_sorted, cap);
     NF_AL(c->nsrc_cell, n_cells);
     NF_AL(c->items, cap);
-    NF_AL(c->decomp_d, 1);
+    NF_AL(c->decomp_d, 3);
     NF_AL(c->state, 1);
     NF_AL(c->mom_partial, (int64_t)nf::kMomBlocks * 4);
     NF_AL(c->mom_result, 4);
@@ -359,9 +373,9 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     memset(c->state_h, 0, sizeof(nf::DevState));
     // default launch shape: 4 sinks per lane, 4 warps per block (FP32);
     // the compensated variant keeps 2 sinks per lane to stay clear of spills
-    c->tune = nf_tuning{4, 4, 0, 1};
+    c->tune = nf_tuning{4, 4, 0, 1, 2};
     if (precision == NF_PREC_FP32_COMP) c->tune.sinks_per_lane = 2;
-    if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1;
+    if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1, c->tune.vjp_sinks_per_lane = 1;
     *out = reinterpret_cast<nf_ctx *>(c);
     return NF_OK;
 }
@@ -503,12 +517,13 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_vjp: no binned particles");
     if (c->n > 0 && (!w || !grad_pos)) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: w and grad_pos are required");
-    int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
+    const int K = vjp_k(c);
+    int rc = ensure_decomp(c, K, s);
     if (rc) return rc;
     cudaError_t e;
     if (c->tune.use_graph) {
         std::vector<uint64_t> key = {(uint64_t)(uintptr_t)w, (uint64_t)(uintptr_t)grad_pos, (uint64_t)c->n,
-                                     (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
+                                     (uint64_t)K, (uint64_t)c->tune.warps_per_block,
                                      (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
                                      (uint64_t)c->equal_mass};
         e = run_graph(c, c->g_vjp, key, [&](cudaStream_t cs) { return enqueue_vjp(c, w, grad_pos, cs); }, s);
@@ -697,8 +712,8 @@ int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
 int nf_set_tuning(nf_ctx *ctx, const nf_tuning *t) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !t) return fail(c, NF_EINVAL, "nf_set_tuning: ctx and t are required");
-    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32]");
-    if (c->precision == NF_PREC_FP64_REF && t->sinks_per_lane != 1)
+    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32], vjp_sinks_per_lane in {0,1,2,4}");
+    if (c->precision == NF_PREC_FP64_REF && (t->sinks_per_lane != 1 || t->vjp_sinks_per_lane > 1))
         return fail(c, NF_EINVAL, "nf_set_tuning: FP64 reference contexts use one sink per lane");
     c->tune = *t;
     return NF_OK;
@@ -723,7 +738,7 @@ int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
     const int ws[] = {4, 8};
     for (int k : ks) {
         if (c->precision == NF_PREC_FP64_REF && k != 1) continue;
-        for (int w : ws) cands.push_back(nf_tuning{k, w, 0, c->tune.use_graph});
+        for (int w : ws) cands.push_back(nf_tuning{k, w, 0, c->tune.use_graph, c->tune.vjp_sinks_per_lane});
     }
     float *acc = nullptr;
     NF_CK(c, dalloc(&acc, 3 * (c->n > 0 ? c->n : 1)));

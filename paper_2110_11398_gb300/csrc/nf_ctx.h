@@ -53,8 +53,9 @@ struct Ctx {
     // work list
     int *nsrc_cell = nullptr;                      // [n_cells]
     WorkItem *items = nullptr;                     // [capacity]
-    Decomp *decomp_d = nullptr;
-    int decomp_k = 0;
+    Decomp *decomp_d = nullptr;                    // [3]: tables for K = 1, 2, 4
+    int decomp_built = 0;                          // bit i: table i uploaded
+    int decomp_k = 0;                              // K of the next work list
     DevState *state = nullptr;
     DevState *state_h = nullptr;                   // pinned mirror
 
@@ -73,7 +74,7 @@ struct Ctx {
     std::vector<double> box_gm;                    // per-box G m (nf_set_box_masses), empty = unset
     int have_momentum = 0;
 
-    nf_tuning tune{4, 4, 0, 1};
+    nf_tuning tune{4, 4, 0, 1, 2};
     cudaStream_t cap_stream = nullptr;             // private capture stream
     GraphSlot g_fwd, g_vjp;
     cudaStream_t last_stream = nullptr;

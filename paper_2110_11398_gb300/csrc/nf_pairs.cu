@@ -674,6 +674,7 @@ __global__ void __launch_bounds__(512) k_vjp(PairArgs a) {
 #pragma unroll
             for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
             const int n_it = (npair - sp + S - 1) >> log2s;
+#pragma unroll 1
             for (int it = 0; it < n_it; ++it) {
                 const int pp = sp + (it << log2s);
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
@@ -1059,7 +1060,7 @@ cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
     a.count = c->count;
     a.cell_start = c->cell_start;
     a.nsrc_cell = c->nsrc_cell;
-    a.decomp = c->decomp_d;
+    a.decomp = c->decomp_d + (c->decomp_k == 1 ? 0 : (c->decomp_k == 2 ? 1 : 2));
     a.st = c->state;
     a.items = c->items;
     const unsigned blocks = (unsigned)((c->n_cells + 255) / 256);

@@ -307,15 +307,17 @@ class NearField:
         t = N.nf_tuning()
         N.check(self._lib.nf_get_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_get_tuning")
         return {"sinks_per_lane": t.sinks_per_lane, "warps_per_block": t.warps_per_block,
-                "blocks_per_sm": t.blocks_per_sm, "use_graph": t.use_graph}
+                "blocks_per_sm": t.blocks_per_sm, "use_graph": t.use_graph,
+                "vjp_sinks_per_lane": t.vjp_sinks_per_lane}
 
     def set_tuning(self, sinks_per_lane=None, warps_per_block=None, blocks_per_sm=None,
-                   use_graph=None) -> None:
+                   use_graph=None, vjp_sinks_per_lane=None) -> None:
         cur = self.tuning
         t = N.nf_tuning(cur["sinks_per_lane"] if sinks_per_lane is None else sinks_per_lane,
                         cur["warps_per_block"] if warps_per_block is None else warps_per_block,
                         cur["blocks_per_sm"] if blocks_per_sm is None else blocks_per_sm,
-                        cur["use_graph"] if use_graph is None else int(use_graph))
+                        cur["use_graph"] if use_graph is None else int(use_graph),
+                        cur["vjp_sinks_per_lane"] if vjp_sinks_per_lane is None else vjp_sinks_per_lane)
         N.check(self._lib.nf_set_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_set_tuning")
 
     def autotune(self, reps: int = 2, cache: str | None = None) -> dict:

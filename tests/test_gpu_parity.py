@@ -540,3 +540,38 @@ def test_batched_vjp_bit_identical_to_plain(dev):
         idx = np.arange(0, b.n, 11)
         ref = oracle.vjp(b.pos, w[o0:o1].cpu().numpy(), b.L, b.cpd, b.R, b.eps, m0=b.gm, sinks=idx)
         assert_parity(gp[idx], ref, what=f"batched vjp {b.name}")
+
+
+@pytest.mark.parametrize("kv", [0, 1, 2, 4])
+def test_vjp_launch_shapes(dev, kv):
+    """The adjoint kernel's own sinks per lane (0: as the forward kernel),
+    alternating with forward calls of another K in one context."""
+    box = synth.tiny(seed=2)
+    w = synth.cotangent(box.n, 9)
+    ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    refa = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    nf = make_nf(box, dev, sinks_per_lane=4, vjp_sinks_per_lane=kv)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    wt = torch.from_numpy(w).to(dev)
+    for _ in range(2):
+        a = nf.accel().cpu().numpy()
+        g = nf.vjp(wt).cpu().numpy()
+        assert_parity(a, refa, what=f"forward next to vjp K={kv}")
+        assert_parity(g, ref, what=f"vjp K={kv}")
+    assert nf.tuning["vjp_sinks_per_lane"] == kv
+    nf.close()
+
+
+def test_default_launch_shapes(dev):
+    """Defaults: forward K = 4; the adjoint K = 2 (its fastest on the
+    clustered adjoint box, 94 ms against 104 ms at K = 4); one sink per lane
+    for FP64."""
+    box = synth.tiny()
+    nf = make_nf(box, dev)
+    t = nf.tuning
+    assert (t["sinks_per_lane"], t["warps_per_block"], t["vjp_sinks_per_lane"]) == (4, 4, 2)
+    nf.close()
+    nf = make_nf(box, dev, "fp64")
+    t = nf.tuning
+    assert (t["sinks_per_lane"], t["vjp_sinks_per_lane"]) == (1, 1)
+    nf.close()

@@ -146,7 +146,7 @@ def test_spline_vjp(dev, K, radius):
     eps_s = 2.5 * box.eps if radius == "production" else 0.8 * spacing(box)
     w = synth.cotangent(box.n, 11)
     ref = oracle.vjp(box.pos, w, box.L, box.cpd, box.R, eps_s, m0=box.gm, law="spline")
-    got = run_vjp(box, dev, eps_s, w, sinks_per_lane=K)
+    got = run_vjp(box, dev, eps_s, w, vjp_sinks_per_lane=K)
     check(got, ref, f"spline vjp K={K} {radius}")
     assert np.abs(got.astype(np.float64).sum(0)).max() <= 1e-5 * np.abs(got).sum()
 
