@@ -53,8 +53,8 @@ def dist_env():
 # dram__bytes_write.sum) from one ncu capture each, with the sha256 of the
 # kernel source they were taken on; a changed source reports null.
 TRAFFIC_CAPTURES = {
-    ("early_256c_cpd65", "k_pairs"): (5.53e9 + 0.26632e9, "e96ebc8e6f61f7ff6680e16752189133456437af99928bf685cb7388065468f3"),
-    ("late_512c_cpd129", "k_pairs"): (55.75e9 + 2.65e9, "e96ebc8e6f61f7ff6680e16752189133456437af99928bf685cb7388065468f3"),
+    ("early_256c_cpd65", "k_pairs"): (5.56e9 + 0.26576e9, "b77cebcce45349ad9ecf00ed2055567f90fecf0c0be0f62882a0150ec8bf41dc"),
+    ("late_512c_cpd129", "k_pairs"): (56.75e9 + 2.66e9, "b77cebcce45349ad9ecf00ed2055567f90fecf0c0be0f62882a0150ec8bf41dc"),
 }
 
 
