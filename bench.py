@@ -253,7 +253,7 @@ def run_reference(args):
             return oracle.vjp(pos64, w, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, cid=cid)
         return oracle.accel(pos64, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx, cid=cid)
 
-    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step = args.ref_seconds or max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     rng = np.random.default_rng(7)
     tot_inter, tot_t, sizes = 0, 0.0, []
     for step in range(args.warmup + args.steps):
@@ -899,6 +899,8 @@ def main(argv=None):
     ap.add_argument("--sinks-per-lane", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=0.0,
+                    help="oracle seconds per step of the reference arm (default: 2-20 s, sized to the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
