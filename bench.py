@@ -848,9 +848,16 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         rate, sample, got, ref = run.oracle_check(args.cpu_seconds)
-        e = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+        dn = np.linalg.norm(got - ref, axis=1)
+        rn = np.linalg.norm(ref, axis=1)
+        e = dn / np.maximum(rn, 1e-300)
+        rms = float(np.sqrt(np.mean(rn * rn)))
+        # fractional errors blow up where the reference nearly cancels: also
+        # the error against the rms force, and how many sinks are that small
         err = {"median": float(np.median(e)), "p99.9": float(np.quantile(e, 0.999)),
-               "max": float(e.max()), "sinks": int(len(e))}
+               "max": float(e.max()), "sinks": int(len(e)),
+               "max_over_rms": float(dn.max() / rms) if rms > 0 else 0.0,
+               "tiny_reference_sinks": int(np.sum(rn < 1e-3 * rms))}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": sample, "single_core_tiny": oracle_single_core_tiny()}
 
