@@ -23,7 +23,7 @@
 // 162 transforms per step instead of 330, and the tensor is stored only for
 // x-exponents <= 2.
 // The tensor is split as in Ewald's method: d^q [erfc(alpha r)/r] summed in
-// real space over the few lattice vectors it reaches (on the host, once), and
+// real space over the few lattice vectors it reaches (once, on the GPU), and
 // the rest, (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q, written straight into
 // its discrete Fourier transform. cuFFT does the transforms; the multipoles,
 // the per-frequency products and the Taylor gradient are kernels here.
@@ -34,7 +34,6 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
-#include <thread>
 #include <vector>
 
 #include "nf_ctx.h"
@@ -101,132 +100,129 @@ struct FarState {
 
 namespace {
 
-// ------------------------------------------------------------ host: short-range tensor
-// (1/r d/dr)^n of the two radial functions of the real-space part.
-// erfc(alpha r)/r: h_n = (-1)^n B_n, B_0 = erfc(alpha r)/r,
-//   B_n = ((2n - 1) B_{n-1} + (2 alpha^2)^n exp(-alpha^2 r^2) / (alpha sqrt(pi))) / r^2.
-void radial_erfc(double r, double alpha, int n_max, double *h) {
-    const double gauss = std::exp(-alpha * alpha * r * r) / (alpha * std::sqrt(M_PI));
-    double B = std::erfc(alpha * r) / r, pw = 1.0;
-    h[0] = B;
-    for (int n = 1; n <= n_max; ++n) {
-        pw *= 2.0 * alpha * alpha;
-        B = ((2 * n - 1) * B + pw * gauss) / (r * r);
-        h[n] = (n & 1) ? -B : B;
-    }
-}
+// ------------------------------------------------------------ short-range tensor
+// Lattice vectors of the real-space part: every integer s with
+// |s| < r_cut, plus the near-field block [-R, R]^3, grouped by the grid cell
+// s mod P that they add to (host bookkeeping; the arithmetic is in
+// k_far_realspace). The near flag marks the vectors whose image the near
+// field already has.
+struct RealSpaceVectors {
+    std::vector<int4> vec;        // (x, y, z, near)
+    std::vector<int> first;       // CSR over cells: vec[first[t] .. first[t+1])
+    std::vector<int64_t> cell;    // grid cell of each group
+};
 
-// -erf(alpha r)/r (the near image: erfc/r minus the 1/r that the near field
-// already has), from its power series, which has no cancellation at r ~ 1/alpha:
-//   h_n = -(2 alpha / sqrt(pi)) (-2 alpha^2)^n sum_j (-alpha^2 r^2)^j / (j! (2n + 2j + 1)).
-void radial_minus_erf(double r, double alpha, int n_max, double *h) {
-    const double x = alpha * alpha * r * r;
-    double lead = -2.0 * alpha / std::sqrt(M_PI);
-    for (int n = 0; n <= n_max; ++n) {
-        double t = 1.0, s = 0.0;
-        for (int j = 0; j < 400; ++j) {
-            const double term = t / (2.0 * (n + j) + 1.0);
-            s += term;
-            if (j > x && std::fabs(term) < 1e-19 * std::fabs(s)) break;
-            t *= -x / (j + 1);
-        }
-        h[n] = lead * s;
-        lead *= -2.0 * alpha * alpha;
-    }
-}
-
-// All Cartesian derivatives d^(a,b,c) f at v, |(a,b,c)| <= mi.n, of a radial
-// function given h_n = (1/r d/dr)^n f: the Hermite-type recursion
-//   H^(n)_{a,b,c} = v_x H^(n+1)_{a-1,b,c} + (a - 1) H^(n+1)_{a-2,b,c}
-// (likewise along y and z), H^(n)_000 = h_n, d^(a,b,c) f = H^(0)_abc.
-void cartesian_derivs(const double v[3], const double *h, const MultiIndex &mi,
-                      std::vector<double> &H, double *out) {
-    const int n = mi.n, N = mi.size();
-    H.resize((size_t)(n + 1) * N);
-    for (int i = 0; i < N; ++i) {
-        const int a = mi.a[i], b = mi.b[i], c = mi.c[i], deg = a + b + c;
-        for (int l = 0; l + deg <= n; ++l) {
-            double val;
-            if (deg == 0) {
-                val = h[l];
-            } else if (c > 0) {
-                val = v[2] * H[(size_t)(l + 1) * N + mi.at(a, b, c - 1)];
-                if (c > 1) val += (c - 1) * H[(size_t)(l + 1) * N + mi.at(a, b, c - 2)];
-            } else if (b > 0) {
-                val = v[1] * H[(size_t)(l + 1) * N + mi.at(a, b - 1, c)];
-                if (b > 1) val += (b - 1) * H[(size_t)(l + 1) * N + mi.at(a, b - 2, c)];
-            } else {
-                val = v[0] * H[(size_t)(l + 1) * N + mi.at(a - 1, b, c)];
-                if (a > 1) val += (a - 1) * H[(size_t)(l + 1) * N + mi.at(a - 2, b, c)];
-            }
-            H[(size_t)l * N + i] = val;
-        }
-    }
-    for (int i = 0; i < N; ++i) out[i] += H[i];
-}
-
-// Real-space part of the tensor: every integer lattice vector s with
-// |s| < r_cut contributes d^q[erfc(alpha r)/r](s) to grid cell s mod P; the
-// near-field vectors (s in [-R, R]^3) contribute d^q[-erf(alpha r)/r](s).
-// Returns the touched cells and their nq values. Vectors are grouped by cell
-// and each cell is summed by one thread in a fixed order, so the result does
-// not depend on the thread count.
-void real_space_part(int P, int R, double alpha, double r_cut, const MultiIndex &mq,
-                     const std::vector<int> &keep, std::vector<int64_t> &cells, std::vector<double> &vals) {
-    const int nq = mq.size(), nk = (int)keep.size();
+RealSpaceVectors real_space_vectors(int P, int R, double r_cut) {
     const int smax = (int)std::ceil(r_cut);
-    struct Vec { int64_t cell; int x, y, z; };
-    std::vector<Vec> vecs;
+    struct V { int64_t cell; int x, y, z, near; };
+    std::vector<V> all;
     for (int x = -smax; x <= smax; ++x)
         for (int y = -smax; y <= smax; ++y)
             for (int z = -smax; z <= smax; ++z) {
-                const bool near = std::abs(x) <= R && std::abs(y) <= R && std::abs(z) <= R;
+                const int near = std::abs(x) <= R && std::abs(y) <= R && std::abs(z) <= R;
                 if (!near && std::sqrt((double)x * x + (double)y * y + (double)z * z) >= r_cut) continue;
                 const int64_t g = ((int64_t)(((x % P) + P) % P) * P + ((y % P) + P) % P) * P + ((z % P) + P) % P;
-                vecs.push_back({g, x, y, z});
+                all.push_back({g, x, y, z, near});
             }
-    std::stable_sort(vecs.begin(), vecs.end(), [](const Vec &u, const Vec &v) { return u.cell < v.cell; });
-    std::vector<size_t> first;   // start of each cell's run in vecs
-    cells.clear();
-    for (size_t i = 0; i < vecs.size(); ++i)
-        if (i == 0 || vecs[i].cell != vecs[i - 1].cell) { first.push_back(i); cells.push_back(vecs[i].cell); }
-    first.push_back(vecs.size());
-    vals.assign(cells.size() * (size_t)nk, 0.0);
-    const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t)
-        th.emplace_back([&, t]() {
-            std::vector<double> H, full(nq);
-            double h[64];
-            for (size_t g = t; g < cells.size(); g += nt) {
-                std::fill(full.begin(), full.end(), 0.0);
-                for (size_t i = first[g]; i < first[g + 1]; ++i) {
-                    const Vec &v = vecs[i];
-                    const double sv[3] = {(double)v.x, (double)v.y, (double)v.z};
-                    const double r = std::sqrt(sv[0] * sv[0] + sv[1] * sv[1] + sv[2] * sv[2]);
-                    const bool near = std::abs(v.x) <= R && std::abs(v.y) <= R && std::abs(v.z) <= R;
-                    if (near) radial_minus_erf(r, alpha, mq.n, h);
-                    else radial_erfc(r, alpha, mq.n, h);
-                    cartesian_derivs(sv, h, mq, H, full.data());
-                }
-                for (int k = 0; k < nk; ++k) vals[g * (size_t)nk + k] = full[keep[k]];
-            }
-        });
-    for (auto &x : th) x.join();
+    std::stable_sort(all.begin(), all.end(), [](const V &u, const V &v) { return u.cell < v.cell; });
+    RealSpaceVectors out;
+    for (size_t i = 0; i < all.size(); ++i) {
+        if (i == 0 || all[i].cell != all[i - 1].cell) {
+            out.first.push_back((int)i);
+            out.cell.push_back(all[i].cell);
+        }
+        out.vec.push_back(make_int4(all[i].x, all[i].y, all[i].z, all[i].near));
+    }
+    out.first.push_back((int)all.size());
+    return out;
 }
 
-// ------------------------------------------------------------ kernels
-__global__ void k_far_scatter(const double *__restrict__ vals, const int64_t *__restrict__ cells,
-                              int64_t n_cells_touched, int nq, int64_t ncell, double *__restrict__ grid) {
-    const int64_t total = n_cells_touched * nq;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / nq;
-        const int q = (int)(i - t * nq);
-        grid[(int64_t)q * ncell + cells[t]] = vals[i];
+// Real-space part of the tensor, one block per touched grid cell, its
+// lattice vectors in a fixed order. For a vector s (cell units, r = |s|):
+//   radial factors h_n = (1/r d/dr)^n f, n <= Q, of f = erfc(alpha r)/r,
+//     h_n = (-1)^n B_n, B_0 = erfc(alpha r)/r,
+//     B_n = ((2n-1) B_{n-1} + (2 alpha^2)^n exp(-alpha^2 r^2)/(alpha sqrt(pi))) / r^2;
+//   or, for the near image, of f = -erf(alpha r)/r (its series, which does
+//   not cancel at r ~ 1/alpha and is finite at r = 0):
+//     h_n = -(2 alpha/sqrt(pi)) (-2 alpha^2)^n sum_j (-alpha^2 r^2)^j / (j! (2n+2j+1));
+//   Cartesian derivatives by the Hermite-type recursion
+//     H^(n)_{a,b,c} = z H^(n+1)_{a,b,c-1} + (c-1) H^(n+1)_{a,b,c-2} (likewise y, x),
+//     H^(n)_000 = h_n, d^(a,b,c) f = H^(0)_abc,
+//   one degree at a time in shared memory. The kept components of the
+//   cell's sum go to the zeroed grid (component-major).
+__global__ void k_far_realspace(const int4 *__restrict__ vec, const int *__restrict__ first,
+                                const int64_t *__restrict__ cell, int ncells_t, int Q, int nq,
+                                const int *__restrict__ qa, const int *__restrict__ qb, const int *__restrict__ qc,
+                                const int *__restrict__ qpos, const int *__restrict__ keep, int nk, double alpha,
+                                int64_t ncell, double *__restrict__ grid) {
+    extern __shared__ double fsm[];
+    double *H = fsm;                               // [(Q+1)][nq]
+    double *full = H + (size_t)(Q + 1) * nq;       // [nq]
+    double *h = full + nq;                         // [Q+1]
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int Q1 = Q + 1;
+    for (int ct = blockIdx.x; ct < ncells_t; ct += gridDim.x) {
+        for (int i = t; i < nq; i += nt) full[i] = 0.0;
+        for (int v = first[ct]; v < first[ct + 1]; ++v) {
+            const int4 s4 = vec[v];
+            const double sx = s4.x, sy = s4.y, sz = s4.z;
+            const double r = sqrt(sx * sx + sy * sy + sz * sz);
+            __syncthreads();
+            if (s4.w) {   // near image: the series of -erf(alpha r)/r, one n per thread
+                const double x = alpha * alpha * r * r;
+                for (int n = t; n <= Q; n += nt) {
+                    double term = 1.0, sum = 0.0;
+                    for (int j = 0; j < 400; ++j) {
+                        const double u = term / (2.0 * (n + j) + 1.0);
+                        sum += u;
+                        if (j > x && fabs(u) < 1e-19 * fabs(sum)) break;
+                        term *= -x / (j + 1);
+                    }
+                    h[n] = -2.0 * alpha / sqrt(M_PI) * pow(-2.0 * alpha * alpha, (double)n) * sum;
+                }
+            } else if (t == 0) {
+                const double gauss = exp(-alpha * alpha * r * r) / (alpha * sqrt(M_PI));
+                double B = erfc(alpha * r) / r, pw = 1.0;
+                h[0] = B;
+                for (int n = 1; n <= Q; ++n) {
+                    pw *= 2.0 * alpha * alpha;
+                    B = ((2 * n - 1) * B + pw * gauss) / (r * r);
+                    h[n] = (n & 1) ? -B : B;
+                }
+            }
+            __syncthreads();
+            for (int deg = 0; deg <= Q; ++deg) {
+                const int i0 = deg * (deg + 1) * (deg + 2) / 6, cnt = (deg + 1) * (deg + 2) / 2;
+                const int levels = Q1 - deg;
+                for (int w = t; w < cnt * levels; w += nt) {
+                    const int i = i0 + w % cnt, n = w / cnt;
+                    const int a = qa[i], b = qb[i], c = qc[i];
+                    double val;
+                    if (deg == 0) {
+                        val = h[n];
+                    } else if (c > 0) {
+                        val = sz * H[(size_t)(n + 1) * nq + qpos[(a * Q1 + b) * Q1 + c - 1]];
+                        if (c > 1) val += (c - 1) * H[(size_t)(n + 1) * nq + qpos[(a * Q1 + b) * Q1 + c - 2]];
+                    } else if (b > 0) {
+                        val = sy * H[(size_t)(n + 1) * nq + qpos[(a * Q1 + b - 1) * Q1 + c]];
+                        if (b > 1) val += (b - 1) * H[(size_t)(n + 1) * nq + qpos[(a * Q1 + b - 2) * Q1 + c]];
+                    } else {
+                        val = sx * H[(size_t)(n + 1) * nq + qpos[((a - 1) * Q1 + b) * Q1 + c]];
+                        if (a > 1) val += (a - 1) * H[(size_t)(n + 1) * nq + qpos[((a - 2) * Q1 + b) * Q1 + c]];
+                    }
+                    H[(size_t)n * nq + i] = val;
+                }
+                __syncthreads();
+            }
+            for (int i = t; i < nq; i += nt) full[i] += H[i];
+        }
+        __syncthreads();
+        for (int k = t; k < nk; k += nt) grid[(int64_t)k * ncell + cell[ct]] = full[keep[k]];
+        __syncthreads();
     }
 }
 
+// ------------------------------------------------------------ kernels
 // Long-range part, added in Fourier space: for frequency w (cuFFT R2C layout
 // [x][y][z <= P/2]) and every alias m = w + G P with 0 < |k| < k_cut,
 // k = 2 pi m / P:  Dh_q(w) += (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q.
@@ -615,23 +611,39 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             const double k_cut = (13.0 + 0.5 * mq.n) * alpha;
             int *da = nullptr;
             if ((e = upload(&da, dabc))) return cuda_err(e, "tables");
-            // real-space part (host), scattered into a zeroed FP64 grid
-            std::vector<int64_t> cells;
-            std::vector<double> vals;
-            real_space_part(P, c->R, alpha, r_cut, mq, stored, cells, vals);
-            double *grid = nullptr, *dvals = nullptr;
-            int64_t *dcells = nullptr;
+            // real-space part: lattice vectors grouped by grid cell (host), their
+            // derivatives summed on the GPU into a zeroed FP64 grid
+            const RealSpaceVectors rs = real_space_vectors(P, c->R, r_cut);
+            double *grid = nullptr;
+            int4 *dvec = nullptr;
+            int *dfirst = nullptr, *dq = nullptr, *dqpos = nullptr, *dkeep = nullptr;
+            int64_t *dcell = nullptr;
             if ((e = dmalloc(&T.Dh, (size_t)f->nd * T.nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
-            if ((e = dmalloc(&grid, (size_t)f->nd * T.ncell)) || (e = upload(&dvals, vals)) ||
-                (e = upload(&dcells, cells))) {
-                cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+            auto free_rs = [&]() {
+                cudaFree(da); cudaFree(grid); cudaFree(dvec); cudaFree(dfirst); cudaFree(dq); cudaFree(dqpos);
+                cudaFree(dkeep); cudaFree(dcell);
+            };
+            std::vector<int> qall(3 * (size_t)mq.size());
+            for (int i = 0; i < mq.size(); ++i) {
+                qall[i] = mq.a[i]; qall[mq.size() + i] = mq.b[i]; qall[2 * (size_t)mq.size() + i] = mq.c[i];
+            }
+            if ((e = dmalloc(&grid, (size_t)f->nd * T.ncell)) || (e = upload(&dvec, rs.vec)) ||
+                (e = upload(&dfirst, rs.first)) || (e = upload(&dcell, rs.cell)) || (e = upload(&dq, qall)) ||
+                (e = upload(&dqpos, mq.pos)) || (e = upload(&dkeep, stored))) {
+                free_rs();
                 return cuda_err(e, "tensor");
             }
             e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nd * T.ncell, s);
             if (!e) {
-                k_far_scatter<<<grid_blocks((int64_t)cells.size() * f->nd, 256, c->sm_count, 8), 256, 0, s>>>(
-                    dvals, dcells, (int64_t)cells.size(), f->nd, T.ncell, grid);
-                e = cudaGetLastError();
+                const size_t smem = sizeof(double) * ((size_t)(mq.n + 1) * mq.size() + mq.size() + mq.n + 1);
+                e = cudaFuncSetAttribute(k_far_realspace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (!e) {
+                    const int ncells_t = (int)rs.cell.size();
+                    k_far_realspace<<<std::min(ncells_t, c->sm_count * 2), 256, smem, s>>>(
+                        dvec, dfirst, dcell, ncells_t, mq.n, mq.size(), dq, dq + mq.size(), dq + 2 * mq.size(), dqpos,
+                        dkeep, f->nd, alpha, T.ncell, grid);
+                    e = cudaGetLastError();
+                }
             }
             // the tensor's components are transformed 64 at a time, the rest by a
             // second plan: chunk starts stay at even component offsets, which
@@ -664,7 +676,7 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             if (!e) e = cudaStreamSynchronize(s);
             if (plan) cufftDestroy(plan);
             if (plan_rest) cufftDestroy(plan_rest);
-            cudaFree(da); cudaFree(grid); cudaFree(dvals); cudaFree(dcells);
+            free_rs();
             if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
             if (e) return cuda_err(e, "tensor");
             // per-step plans of this size (reduced components)
