@@ -805,7 +805,9 @@ def run_ours(args):
         p = run.far_order
         nfreq = run.far_frequencies()
         nr = (p + 1) ** 2                      # reduced multipoles / Taylor coefficients
-        conv_flops = 8.0 * nfreq * nr * nr     # complex FP64 multiply-add per (k, m, frequency)
+        # one real x complex FP64 multiply-add (2 FMAs, 4 flops) per (k, m, frequency):
+        # the transformed tensor is i^|q| times a real function (parity of the order)
+        conv_flops = 4.0 * nfreq * nr * nr
         conv_ms = float(np.mean(far_conv_ms))
         fp64_peak = fp64_peak_tflops(props.multi_processor_count, sm_max)
         extra["far_field"] = {

@@ -22,6 +22,11 @@
 // With p = 8 that is 81 x 81 products per frequency instead of 165 x 165,
 // 162 transforms per step instead of 330, and the tensor is stored only for
 // x-exponents <= 2.
+// The tensor is real and has the parity of its order, D_q(-d) = (-1)^|q|
+// D_q(d) (1/r is even, and the image sum and the near block are symmetric),
+// so its transform is i^|q| times a real function E_q. Only E_q is kept, and
+// T_k = i^|k| sum_m E_{k+m} (i^|m| W_m): a real number times a complex one per
+// product, half the arithmetic and half the storage of complex products.
 // The tensor is split as in Ewald's method: d^q [erfc(alpha r)/r] summed in
 // real space over the few lattice vectors it reaches (once, on the GPU), and
 // the rest, (4 pi / k^2) exp(-k^2 / 4 alpha^2) (i k)^q, written straight into
@@ -68,7 +73,7 @@ struct MultiIndex {
 struct FarTensor {
     int P = 0;
     int64_t ncell = 0, nfreq = 0;
-    cufftDoubleComplex *Dh = nullptr;  // [nd][nfreq] tensor, x-exponent <= 2
+    double *E = nullptr;               // [nd][nfreq] i^-|q| x transformed tensor, x-exponent <= 2
     cufftHandle r2c = 0, c2r = 0;      // nr components at a time
     bool r2c_ok = false, c2r_ok = false;
 };
@@ -94,6 +99,14 @@ struct FarState {
     int *gptr = nullptr, *gcol = nullptr;
     double *gval = nullptr, *gbg = nullptr;
     int *conv_add = nullptr;           // [nr][nr] position of k + m among the stored tensor components
+    int *rdeg = nullptr;               // [nr] order |m| of each reduced component
+    // gradient terms |j| <= p - 1: positions of j + e_x, j + e_y, j + e_z among
+    // the multi-indices of order <= p, and 1 / j!
+    int nterm = 0;
+    int4 *tix = nullptr;
+    float *tfac = nullptr;
+    float4 *tc = nullptr;              // [max ncell][nterm] completed coefficients (scratch, box by box)
+    int *scell = nullptr;              // [capacity] cell of each sorted particle (scratch)
     std::vector<FarTensor> tensors;
     std::vector<FarBox> boxes;
 };
@@ -264,6 +277,25 @@ __global__ void k_far_longrange(cufftDoubleComplex *__restrict__ Dh, int P, int6
     }
 }
 
+// The transformed tensor is i^|q| times a real function (parity of the
+// order); E_q = i^-|q| Dh_q keeps that real function. What is dropped, the
+// other part, is rounding: about 1e-16 of the kept one.
+__global__ void k_far_realify(const cufftDoubleComplex *__restrict__ Dh, double *__restrict__ E, int64_t nfreq,
+                              int64_t total, const int *__restrict__ qa, const int *__restrict__ qb,
+                              const int *__restrict__ qc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(i / nfreq);
+        const cufftDoubleComplex d = Dh[i];
+        switch ((qa[q] + qb[q] + qc[q]) & 3) {   // i^-|q| d, real part
+            case 0: E[i] = d.x; break;
+            case 1: E[i] = d.y; break;
+            case 2: E[i] = -d.x; break;
+            default: E[i] = -d.y; break;
+        }
+    }
+}
+
 // Multipoles: one block per cell, 128 threads. A tile of up to 128 sorted
 // records is staged with each particle's powers x^e, y^e, z^e (e <= p,
 // particle-major so that a warp reading one particle's powers hits distinct
@@ -325,13 +357,23 @@ __global__ void __launch_bounds__(kFarThreads) k_far_multipoles(
     }
 }
 
-// Per-frequency products T_k(w) = sum_m D_{k+m}(w) W_m(w) over the reduced
-// k and m: a block takes 32 consecutive frequencies (one per lane); W_m(w) is
-// staged in shared memory; warp y of the block computes k = y, y + blockDim.y, ...
-__global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
-                               const cufftDoubleComplex *__restrict__ Wh,
+// i^n v, exact (a swap and sign changes).
+__device__ __forceinline__ double2 times_i_pow(double2 v, int n) {
+    switch (n & 3) {
+        case 0: return v;
+        case 1: return make_double2(-v.y, v.x);
+        case 2: return make_double2(-v.x, -v.y);
+        default: return make_double2(v.y, -v.x);
+    }
+}
+
+// Per-frequency products T_k(w) = i^|k| sum_m E_{k+m}(w) (i^|m| W_m(w)) over
+// the reduced k and m (E real: two FP64 FMAs per product): a block takes 32
+// consecutive frequencies (one per lane); i^|m| W_m(w) is staged in shared
+// memory; warp y of the block computes k = y, y + blockDim.y, ...
+__global__ void k_far_convolve(const double *__restrict__ E, const cufftDoubleComplex *__restrict__ Wh,
                                cufftDoubleComplex *__restrict__ Th, int64_t nfreq, int nr,
-                               const int *__restrict__ add) {
+                               const int *__restrict__ add, const int *__restrict__ rdeg) {
     extern __shared__ double2 cm[];   // [nr][32]
     const int lane = threadIdx.x, wy = threadIdx.y, ny = blockDim.y;
     for (int64_t f0 = (int64_t)blockIdx.x * 32; f0 < nfreq; f0 += (int64_t)gridDim.x * 32) {
@@ -342,7 +384,7 @@ __global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
             double2 v = make_double2(0.0, 0.0);
             if (ok) {
                 const cufftDoubleComplex x = Wh[(int64_t)m * nfreq + f];
-                v = make_double2(x.x, x.y);
+                v = times_i_pow(make_double2(x.x, x.y), __ldg(&rdeg[m]));
             }
             cm[m * 32 + lane] = v;
         }
@@ -352,12 +394,12 @@ __global__ void k_far_convolve(const cufftDoubleComplex *__restrict__ Dh,
             const int *ak = add + (int64_t)k * nr;
             if (ok) {
                 for (int m = 0; m < nr; ++m) {
-                    const cufftDoubleComplex d = Dh[(int64_t)__ldg(&ak[m]) * nfreq + f];
+                    const double d = E[(int64_t)__ldg(&ak[m]) * nfreq + f];
                     const double2 x = cm[m * 32 + lane];
-                    re = fma(d.x, x.x, fma(-d.y, x.y, re));
-                    im = fma(d.x, x.y, fma(d.y, x.x, im));
+                    re = fma(d, x.x, re);
+                    im = fma(d, x.y, im);
                 }
-                Th[(int64_t)k * nfreq + f] = make_double2(re, im);
+                Th[(int64_t)k * nfreq + f] = times_i_pow(make_double2(re, im), __ldg(&rdeg[k]));
             }
         }
     }
@@ -369,67 +411,102 @@ __host__ __device__ constexpr int mi_pos(int a, int b, int c) {
     return (a + b + c) * (a + b + c + 1) * (a + b + c + 2) / 6 + c * (a + b + c + 1) - c * (c - 1) / 2 + b;
 }
 
-// Taylor gradient at every particle: one block per cell. The cell's reduced
-// T (inverse transform / CPD^3) are completed to all |k| <= p in FP64 by the
-// harmonic relation, a fixed sparse map (one component per thread) that also
-// carries the background term 4 pi M_tot / CPD^3 (M_tot is the
-// zero-frequency value of W_0), scaled to box units and staged as floats; each thread takes a particle y and sums, over |j| <= p - 1,
-//   (y^j / j!) (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}).
-// The order is a template parameter, so the loops unroll with the
-// coefficient positions as constants and the powers of y in registers.
-template <int P>
-__global__ void __launch_bounds__(kFarThreads) k_far_taylor(
-    const float4 *__restrict__ sorted, const int *__restrict__ cell_start, const int *__restrict__ perm,
-    const double *__restrict__ Tr, int64_t ncell, int np, int nr, const int *__restrict__ gptr,
-    const int *__restrict__ gcol, const double *__restrict__ gval, const double *__restrict__ gbg,
-    const cufftDoubleComplex *__restrict__ w0_dc, double inv_n, double inv_h2, float *__restrict__ acc,
-    int accumulate) {
-    __shared__ double Tred[2 * kFarThreads];
-    __shared__ float Ts[2 * kFarThreads];
+// Completion of the Taylor coefficients, 32 cells per block. The cells'
+// reduced T (inverse transform / CPD^3, FP64) are completed to all |k| <= p
+// by the harmonic relation: a fixed sparse map, which also carries the
+// background term 4 pi M_tot / CPD^3 (M_tot is the zero-frequency value of
+// W_0). They are scaled to box units and written per cell as the terms of
+// the gradient, the float4 (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}) / j! for
+// |j| <= p - 1 (enumeration of mi_pos). The block also writes, for every
+// particle of its cells, the cell's index: the Taylor kernel takes
+// particles, not cells.
+constexpr int kCompCells = 32;
+constexpr int kFarMaxNp = 165;   // multi-indices of order <= 8 (odd: no bank conflicts)
+constexpr int kFarMaxNr = 81;    // reduced components at p = 8
+
+__global__ void __launch_bounds__(kFarThreads) k_far_complete(
+    const double *__restrict__ Tr, const int *__restrict__ cell_start, int64_t ncell, int np, int nr,
+    const int *__restrict__ gptr, const int *__restrict__ gcol, const double *__restrict__ gval,
+    const double *__restrict__ gbg, const cufftDoubleComplex *__restrict__ w0_dc, double inv_n, double inv_h2,
+    int nterm, const int4 *__restrict__ tix, const float *__restrict__ tfac, float4 *__restrict__ Tc,
+    int *__restrict__ scell) {
+    __shared__ double Tred[kFarMaxNr][kCompCells];
+    __shared__ float Tk[kCompCells][kFarMaxNp];
+    __shared__ int cs[kCompCells + 1];
     const int t = threadIdx.x;
     const double bg = 4.0 * M_PI * w0_dc->x * inv_n;   // 4 pi M_tot / CPD^3
-    for (int64_t cell = blockIdx.x; cell < ncell; cell += gridDim.x) {
-        const int s = cell_start[cell], e = cell_start[cell + 1];
-        if (s == e) continue;   // uniform over the block
+    for (int64_t c0 = (int64_t)blockIdx.x * kCompCells; c0 < ncell; c0 += (int64_t)gridDim.x * kCompCells) {
+        const int nc = (int)min((int64_t)kCompCells, ncell - c0);
         __syncthreads();
-        for (int r = t; r < nr; r += kFarThreads) Tred[r] = Tr[(int64_t)r * ncell + cell] * inv_n;
+        for (int i = t; i < nr * kCompCells; i += kFarThreads) {
+            const int r = i / kCompCells, cl = i % kCompCells;
+            Tred[r][cl] = cl < nc ? Tr[(int64_t)r * ncell + c0 + cl] * inv_n : 0.0;
+        }
+        for (int i = t; i <= nc; i += kFarThreads) cs[i] = cell_start[c0 + i];
         __syncthreads();
-        for (int k = t; k < np; k += kFarThreads) {
+        for (int i = t; i < np * kCompCells; i += kFarThreads) {
+            const int k = i / kCompCells, cl = i % kCompCells;
             double v = gbg[k] * bg;
-            for (int q = gptr[k]; q < gptr[k + 1]; ++q) v = fma(gval[q], Tred[gcol[q]], v);
-            Ts[k] = (float)(v * inv_h2);
+            for (int q = gptr[k]; q < gptr[k + 1]; ++q) v = fma(gval[q], Tred[gcol[q]][cl], v);
+            Tk[cl][k] = (float)(v * inv_h2);
         }
         __syncthreads();
-        for (int j = s + t; j < e; j += kFarThreads) {
-            const float4 r = sorted[j];
-            float px[P], py[P], pz[P];   // y^e / e!
-            px[0] = py[0] = pz[0] = 1.f;
+        float4 *out = Tc + c0 * nterm;
+        for (int i = t; i < nc * nterm; i += kFarThreads) {
+            const int cl = i / nterm, j = i - cl * nterm;
+            const int4 x = tix[j];
+            const float w = tfac[j];
+            out[i] = make_float4(Tk[cl][x.x] * w, Tk[cl][x.y] * w, Tk[cl][x.z] * w, 0.f);
+        }
+        for (int cl = 0; cl < nc; ++cl)
+            for (int j = cs[cl] + t; j < cs[cl + 1]; j += kFarThreads) scell[j] = (int)(c0 + cl);
+    }
+}
+
+// Taylor gradient, one thread per particle of the box (sorted order, so a
+// warp takes 32 consecutive particles of one to a few cells, whatever the
+// cells' occupancy): with y the cell-relative position,
+//   a(y) = sum_{|j| <= p-1} y^j (T_{j+e_x}, T_{j+e_y}, T_{j+e_z}) / j!,
+// one 16-byte load per term from the cell's row of the completed
+// coefficients. The order is a template parameter, so the loops unroll with
+// the term positions as constants and the powers of y in registers.
+template <int P>
+__global__ void __launch_bounds__(kFarThreads) k_far_taylor(
+    const float4 *__restrict__ sorted, const int *__restrict__ perm, const int *__restrict__ scell,
+    const float4 *__restrict__ Tc, int64_t p0, int64_t p1, float *__restrict__ acc, int accumulate) {
+    constexpr int NT = P * (P + 1) * (P + 2) / 6;   // terms |j| <= P - 1
+    for (int64_t j = p0 + (int64_t)blockIdx.x * kFarThreads + threadIdx.x; j < p1;
+         j += (int64_t)gridDim.x * kFarThreads) {
+        const float4 r = sorted[j];
+        const float4 *tc = Tc + (int64_t)scell[j] * NT;
+        float px[P], py[P], pz[P];
+        px[0] = py[0] = pz[0] = 1.f;
 #pragma unroll
-            for (int q = 1; q < P; ++q) {
-                px[q] = px[q - 1] * r.x * (1.f / q);
-                py[q] = py[q - 1] * r.y * (1.f / q);
-                pz[q] = pz[q - 1] * r.z * (1.f / q);
-            }
-            float ax = 0.f, ay = 0.f, az = 0.f;
+        for (int q = 1; q < P; ++q) {
+            px[q] = px[q - 1] * r.x;
+            py[q] = py[q - 1] * r.y;
+            pz[q] = pz[q - 1] * r.z;
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
-            for (int a = 0; a < P; ++a)
+        for (int a = 0; a < P; ++a)
 #pragma unroll
-                for (int b = 0; a + b < P; ++b) {
-                    const float xy = px[a] * py[b];
+            for (int b = 0; a + b < P; ++b) {
+                const float xy = px[a] * py[b];
 #pragma unroll
-                    for (int c = 0; a + b + c < P; ++c) {
-                        const float y = xy * pz[c];
-                        ax = fmaf(y, Ts[mi_pos(a + 1, b, c)], ax);
-                        ay = fmaf(y, Ts[mi_pos(a, b + 1, c)], ay);
-                        az = fmaf(y, Ts[mi_pos(a, b, c + 1)], az);
-                    }
+                for (int c = 0; a + b + c < P; ++c) {
+                    const float y = xy * pz[c];
+                    const float4 t = __ldg(&tc[mi_pos(a, b, c)]);
+                    ax = fmaf(y, t.x, ax);
+                    ay = fmaf(y, t.y, ay);
+                    az = fmaf(y, t.z, az);
                 }
-            float *o = acc + 3 * (int64_t)perm[j];
-            if (accumulate) {
-                o[0] += ax; o[1] += ay; o[2] += az;
-            } else {
-                o[0] = ax; o[1] = ay; o[2] = az;
             }
+        float *o = acc + 3 * (int64_t)perm[j];
+        if (accumulate) {
+            o[0] += ax; o[1] += ay; o[2] += az;
+        } else {
+            o[0] = ax; o[1] = ay; o[2] = az;
         }
     }
 }
@@ -459,11 +536,11 @@ void far_release(Ctx *c) {
     FarState *f = c->far;
     if (!f) return;
     void *bufs[] = {f->mabc, f->coef, f->fptr, f->fcol, f->fval, f->gptr, f->gcol, f->gval, f->gbg,
-                    f->conv_add};
+                    f->conv_add, f->rdeg, f->tix, f->tfac, f->tc, f->scell};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (FarTensor &t : f->tensors) {
-        if (t.Dh) cudaFree(t.Dh);
+        if (t.E) cudaFree(t.E);
         if (t.r2c_ok) cufftDestroy(t.r2c);
         if (t.c2r_ok) cufftDestroy(t.c2r);
     }
@@ -571,6 +648,21 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
                 if (e.second != 0.0) { gcol.push_back(e.first); gval.push_back(e.second); }
             gptr.push_back((int)gcol.size());
         }
+        std::vector<int> rdeg(f->nr);
+        for (int r = 0; r < f->nr; ++r) rdeg[r] = mp.a[red[r]] + mp.b[red[r]] + mp.c[red[r]];
+        std::vector<int4> tix;
+        std::vector<float> tfac;
+        for (int i = 0; i < f->np; ++i) {
+            const int a = mp.a[i], b = mp.b[i], cc = mp.c[i];
+            if (a + b + cc > order - 1) break;   // degree-major: the terms are a prefix
+            tix.push_back(make_int4(mp.at(a + 1, b, cc), mp.at(a, b + 1, cc), mp.at(a, b, cc + 1), 0));
+            double fac = 1.0;
+            for (int x = 2; x <= a; ++x) fac *= x;
+            for (int x = 2; x <= b; ++x) fac *= x;
+            for (int x = 2; x <= cc; ++x) fac *= x;
+            tfac.push_back((float)(1.0 / fac));
+        }
+        f->nterm = (int)tix.size();
         for (int k = 0; k < f->nr; ++k)
             for (int m = 0; m < f->nr; ++m) {
                 const int ik = red[k], im = red[m];
@@ -583,7 +675,8 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
         if ((e = upload(&f->mabc, mabc)) || (e = upload(&f->coef, coef)) || (e = upload(&f->fptr, fptr)) ||
             (e = upload(&f->fcol, fcol)) || (e = upload(&f->fval, fval)) || (e = upload(&f->gptr, gptr)) ||
             (e = upload(&f->gcol, gcol)) || (e = upload(&f->gval, gval)) || (e = upload(&f->gbg, gbg)) ||
-            (e = upload(&f->conv_add, add)))
+            (e = upload(&f->conv_add, add)) || (e = upload(&f->rdeg, rdeg)) || (e = upload(&f->tix, tix)) ||
+            (e = upload(&f->tfac, tfac)))
             return cuda_err(e, "tables");
     }
     std::vector<int> dabc(3 * (size_t)f->nd);
@@ -618,11 +711,14 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             int4 *dvec = nullptr;
             int *dfirst = nullptr, *dq = nullptr, *dqpos = nullptr, *dkeep = nullptr;
             int64_t *dcell = nullptr;
-            if ((e = dmalloc(&T.Dh, (size_t)f->nd * T.nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
+            cufftDoubleComplex *Dh = nullptr;   // the transformed tensor while it is built
+            if ((e = dmalloc(&Dh, (size_t)f->nd * T.nfreq))) { cudaFree(da); return cuda_err(e, "tensor"); }
             auto free_rs = [&]() {
-                cudaFree(da); cudaFree(grid); cudaFree(dvec); cudaFree(dfirst); cudaFree(dq); cudaFree(dqpos);
+                cudaFree(grid); cudaFree(dvec); cudaFree(dfirst); cudaFree(dq); cudaFree(dqpos);
                 cudaFree(dkeep); cudaFree(dcell);
+                grid = nullptr; dvec = nullptr; dfirst = dq = dqpos = dkeep = nullptr; dcell = nullptr;
             };
+            auto free_build = [&]() { free_rs(); cudaFree(Dh); cudaFree(da); };
             std::vector<int> qall(3 * (size_t)mq.size());
             for (int i = 0; i < mq.size(); ++i) {
                 qall[i] = mq.a[i]; qall[mq.size() + i] = mq.b[i]; qall[2 * (size_t)mq.size() + i] = mq.c[i];
@@ -630,7 +726,7 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             if ((e = dmalloc(&grid, (size_t)f->nd * T.ncell)) || (e = upload(&dvec, rs.vec)) ||
                 (e = upload(&dfirst, rs.first)) || (e = upload(&dcell, rs.cell)) || (e = upload(&dq, qall)) ||
                 (e = upload(&dqpos, mq.pos)) || (e = upload(&dkeep, stored))) {
-                free_rs();
+                free_build();
                 return cuda_err(e, "tensor");
             }
             e = cudaMemsetAsync(grid, 0, sizeof(double) * (size_t)f->nd * T.ncell, s);
@@ -666,17 +762,27 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             for (int q0 = 0; !e && fr == CUFFT_SUCCESS && q0 < f->nd; q0 += chunk) {
                 stage = "tensor transform: exec";
                 fr = cufftExecD2Z(q0 + chunk <= f->nd ? plan : plan_rest, grid + (size_t)q0 * T.ncell,
-                                  T.Dh + (size_t)q0 * T.nfreq);
+                                  Dh + (size_t)q0 * T.nfreq);
             }
             if (!e && fr == CUFFT_SUCCESS) {
                 k_far_longrange<<<grid_blocks(T.nfreq, 128, c->sm_count, 8), 128, 0, s>>>(
-                    T.Dh, P, T.nfreq, f->nd, da, da + f->nd, da + 2 * f->nd, alpha, k_cut);
+                    Dh, P, T.nfreq, f->nd, da, da + f->nd, da + 2 * f->nd, alpha, k_cut);
                 e = cudaGetLastError();
             }
             if (!e) e = cudaStreamSynchronize(s);
             if (plan) cufftDestroy(plan);
             if (plan_rest) cufftDestroy(plan_rest);
-            free_rs();
+            free_rs();   // the real-space grid goes before the real tensor is allocated
+            // keep the real function E_q = i^-|q| Dh_q
+            if (!e && fr == CUFFT_SUCCESS) e = dmalloc(&T.E, (size_t)f->nd * T.nfreq);
+            if (!e && fr == CUFFT_SUCCESS) {
+                const int64_t total = (int64_t)f->nd * T.nfreq;
+                k_far_realify<<<grid_blocks(total, 256, c->sm_count, 8), 256, 0, s>>>(
+                    Dh, T.E, T.nfreq, total, da, da + f->nd, da + 2 * f->nd);
+                e = cudaGetLastError();
+                if (!e) e = cudaStreamSynchronize(s);
+            }
+            free_build();
             if (fr != CUFFT_SUCCESS) return fft_err(fr, stage);
             if (e) return cuda_err(e, "tensor");
             // per-step plans of this size (reduced components)
@@ -697,6 +803,10 @@ int far_setup(Ctx *c, int order, cudaStream_t s, std::string &err) {
             (e = dmalloc(&X.Th, (size_t)f->nr * T.nfreq)))
             return cuda_err(e, "buffers");
     }
+    int64_t max_cells = 0;
+    for (const FarTensor &T : f->tensors) max_cells = std::max(max_cells, T.ncell);
+    if ((e = dmalloc(&f->tc, (size_t)max_cells * f->nterm)) || (e = dmalloc(&f->scell, (size_t)c->capacity)))
+        return cuda_err(e, "buffers");
     return NF_OK;
 }
 
@@ -732,14 +842,13 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s, std:
     for (const FarBox &X : f->boxes) {
         const FarTensor &T = f->tensors[X.tensor];
         k_far_convolve<<<grid_blocks(T.nfreq, 32, c->sm_count, 4), dim3(32, ny), smem, s>>>(
-            T.Dh, X.Wh, X.Th, T.nfreq, f->nr, f->conv_add);
+            T.E, X.Wh, X.Th, T.nfreq, f->nr, f->conv_add, f->rdeg);
         c->launches += 1;
         if ((e = cudaGetLastError())) return e;
     }
     if ((e = cudaEventRecord(c->ev_far[3], s))) return e;
-    void (*taylor)(const float4 *, const int *, const int *, const double *, int64_t, int, int, const int *,
-                   const int *, const double *, const double *, const cufftDoubleComplex *, double, double,
-                   float *, int) = nullptr;
+    void (*taylor)(const float4 *, const int *, const int *, const float4 *, int64_t, int64_t, float *, int) =
+        nullptr;
     switch (f->p) {
         case 1: taylor = k_far_taylor<1>; break;
         case 2: taylor = k_far_taylor<2>; break;
@@ -750,7 +859,8 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s, std:
         case 7: taylor = k_far_taylor<7>; break;
         default: taylor = k_far_taylor<8>; break;
     }
-    for (const FarBox &X : f->boxes) {
+    for (size_t b = 0; b < f->boxes.size(); ++b) {
+        const FarBox &X = f->boxes[b];
         const FarTensor &T = f->tensors[X.tensor];
         cufftResult fr = cufftSetStream(T.c2r, s);
         if (fr == CUFFT_SUCCESS) fr = cufftExecZ2D(T.c2r, X.Th, X.W);
@@ -758,11 +868,19 @@ cudaError_t far_compute(Ctx *c, float *acc, int accumulate, cudaStream_t s, std:
             fft_fail = "inverse transform of the Taylor coefficients: cuFFT error " + std::to_string((int)fr);
             return cudaErrorUnknown;
         }
-        taylor<<<grid_blocks(T.ncell * kFarThreads, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
-            c->sorted, c->cell_start + X.cell0, c->perm, X.W, T.ncell, f->np, f->nr, f->gptr, f->gcol, f->gval,
-            f->gbg, X.Wh, 1.0 / (double)T.ncell, X.inv_h2, acc, accumulate);
+        // the box's particles are the sorted range [poff[b], poff[b+1]) (its cells are contiguous)
+        const int64_t p0 = c->poff_h[b], p1 = c->poff_h[b + 1];
+        k_far_complete<<<grid_blocks(T.ncell, kCompCells, c->sm_count, 8), kFarThreads, 0, s>>>(
+            X.W, c->cell_start + X.cell0, T.ncell, f->np, f->nr, f->gptr, f->gcol, f->gval, f->gbg, X.Wh,
+            1.0 / (double)T.ncell, X.inv_h2, f->nterm, f->tix, f->tfac, f->tc, f->scell);
         c->launches += 1;
         if ((e = cudaGetLastError())) return e;
+        if (p1 > p0) {
+            taylor<<<grid_blocks(p1 - p0, kFarThreads, c->sm_count, 16), kFarThreads, 0, s>>>(
+                c->sorted, c->perm, f->scell, f->tc, p0, p1, acc, accumulate);
+            c->launches += 1;
+            if ((e = cudaGetLastError())) return e;
+        }
     }
     return cudaEventRecord(c->ev_far[1], s);
 }

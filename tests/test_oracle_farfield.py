@@ -52,6 +52,31 @@ def test_tensor_does_not_depend_on_the_splitting(d):
         assert np.abs(a[sel] - b[sel]).max() <= tol, (d, t)
 
 
+def test_tensor_has_the_parity_of_its_order():
+    """1/r is even, and both the image sum and the near block it leaves out
+    are symmetric, so D_q(-d) = (-1)^|q| D_q(d), and D is periodic in d with
+    period CPD. Its discrete transform over the grid is therefore i^|q| times a
+    real function (what the GPU keeps of it)."""
+    P, R, Q = 5, 2, 10
+    deg = _per_order(Q)
+    for d in ((1, 2, 0), (2, 2, 1), (0, 0, 3), (4, 1, 3)):
+        a = oracle.far_dtensor(d, P, R, 3.5 / P, Q)
+        b = oracle.far_dtensor([-x for x in d], P, R, 3.5 / P, Q)
+        c = oracle.far_dtensor([(-x) % P for x in d], P, R, 3.5 / P, Q)
+        scale = np.abs(a).max()
+        assert np.abs(b - (-1.0) ** deg * a).max() <= 1e-12 * scale, d
+        assert np.abs(c - b).max() <= 1e-12 * scale, d
+    Q = 4
+    deg = _per_order(Q)
+    D = np.zeros((len(deg), P, P, P))
+    for x in range(P):
+        for y in range(P):
+            for z in range(P):
+                D[:, x, y, z] = oracle.far_dtensor([x, y, z], P, R, 3.5 / P, Q)
+    E = (1j ** -deg)[:, None, None, None] * np.fft.rfftn(D, axes=(1, 2, 3))
+    assert np.abs(E.imag).max() <= 1e-13 * np.abs(E.real).max()
+
+
 def test_tensor_is_its_own_derivative():
     """d^(q + e_x) D = d/dx d^q D, by central differences at a non-lattice point."""
     P, Q, h = 7, 10, 1e-5

@@ -57,6 +57,7 @@ MUTANTS = {
     "far_no_background": ("out[0] -= M_PI / (alpha * alpha * V);", "out[0] -= 0.0;"),
     "far_near_image_kept": ("            g_minus_erf(r, alpha, Q, g);\n        } else {",
                             "            g_minus_erf(r, alpha, Q, g);\n            for (int jj = 0; jj <= Q; ++jj) g[jj] *= 0.5;\n        } else {"),
+    "far_near_block_lopsided": ("fabs(s[1]) <= R && fabs(s[2]) <= R;", "fabs(s[1]) <= R && s[2] >= -R && s[2] < R;"),
 }
 
 
@@ -116,6 +117,7 @@ def _run_pins(first_only=False):
         ("vjp_fd", lambda: P.test_vjp_two_body_finite_difference(oracle)),
         ("vjp_spline_fd", lambda: S.test_spline_vjp_central_differences(oracle)),
         ("far_lattice_constant", lambda: F.test_tensor_origin_value_is_the_cubic_lattice_constant(5)),
+        ("far_parity", F.test_tensor_has_the_parity_of_its_order),
         ("far_vs_ewald", F.test_far_plus_near_equals_ewald_and_converges_with_order),
         ("far_cell_shift", F.test_far_field_follows_a_whole_cell_shift),
     ]
