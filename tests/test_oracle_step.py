@@ -99,3 +99,31 @@ def test_kdk_second_order():
 
     e1, e2 = orbit(100), orbit(200)
     assert 3.0 < e1 / e2 < 5.0, (e1, e2)
+
+
+def test_kdk_with_the_far_field_kicks_with_the_total_force():
+    """With the far field on, the step's force is near + far, which for
+    (almost) unsoftened particles is the Ewald force of the periodic box: the
+    acceleration the step returns at its new positions matches the Ewald sum
+    there to the far field's truncation error, and the velocity follows the
+    leapfrog with those forces. Without the far field it misses the other
+    images by far more."""
+    L, cpd, R, eps = 1.0, 7, 2, 1e-7
+    rng = np.random.default_rng(3)
+    n = 80
+    m = 1.0 / n
+    x = rng.random((n, 3)).astype(np.float32)
+    v = (rng.standard_normal((n, 3)) * 0.01).astype(np.float32)
+    dt = 1e-3
+    x1, v1, a1 = oracle.kdk_step(x, v, dt, L, cpd, R, eps, m0=m, far_order=8)
+    a0e = oracle.ewald_accel(x.astype(np.float64), L, m0=m)
+    a1e = oracle.ewald_accel(x1.astype(np.float64), L, m0=m)
+    e = np.linalg.norm(a1 - a1e, axis=1) / np.linalg.norm(a1e, axis=1)
+    assert np.median(e) < 1e-5, np.median(e)
+    v_half = (v.astype(np.float64) + 0.5 * dt * a0e).astype(np.float32)
+    v_e = v_half.astype(np.float64) + 0.5 * dt * a1e
+    scale = dt * np.abs(a1e).max()
+    assert np.abs(v1 - v_e).max() < 1e-5 * scale + 1e-6 * np.abs(v).max()
+    _, _, a1n = oracle.kdk_step(x, v, dt, L, cpd, R, eps, m0=m)
+    en = np.linalg.norm(a1n - a1e, axis=1) / np.linalg.norm(a1e, axis=1)
+    assert np.median(en) > 100 * np.median(e), (np.median(en), np.median(e))
