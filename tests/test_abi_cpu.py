@@ -94,6 +94,20 @@ def test_null_context_calls(lib):
     assert lib.nf_compute_accel_vjp(None, None, None, None) == N.NF_EINVAL
     assert lib.nf_get_stats(None, None) == N.NF_EINVAL
     assert lib.nf_copy_binning(None, None, None, None, None) == N.NF_EINVAL
+    assert lib.nf_compute_accel_f64(None, None, None) == N.NF_EINVAL
+    assert lib.nf_compute_accel_density(None, None, None, None, None) == N.NF_EINVAL
+    assert lib.nf_set_box_masses(None, None) == N.NF_EINVAL
+    assert lib.nf_far_init(None, 8, None) == N.NF_EINVAL
+    assert "nf_far_init" in lib.nf_last_error(None).decode()
+    assert lib.nf_compute_far(None, None, 0, None) == N.NF_EINVAL
+    assert lib.nf_kick(None, None, None, 0.1, None) == N.NF_EINVAL
+    assert lib.nf_drift(None, None, None, 0.1, None) == N.NF_EINVAL
+    assert lib.nf_timestep(None, None, None, 0.25, None, None) == N.NF_EINVAL
+    assert lib.nf_kdk_step(None, None, None, None, None, 0.0, 0.1, None, None) == N.NF_EINVAL
+    assert lib.nf_accel_host(None, None, None, 0.0, 0, None, None, None) == N.NF_EINVAL
+    assert lib.nf_set_tuning(None, None) == N.NF_EINVAL
+    assert lib.nf_get_tuning(None, None) == N.NF_EINVAL
+    assert lib.nf_autotune(None, 1, None, None) == N.NF_EINVAL
 
 
 def test_missing_library_fails_loudly(tmp_path):
