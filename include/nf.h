@@ -214,10 +214,13 @@ NF_API int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, vo
  * fluctuations, the periodic convention of cosmological codes).
  *   order   p in [1, 8] (the paper uses 8)
  * Only the tensor components with x-exponent <= 2 are kept (the tensor is
- * harmonic, which fixes the rest): 409 of them at p = 8, about
- * 8 x 409 CPD^3 bytes in Fourier space (7 GB at CPD = 129), plus as much
- * again while it is built, and 3 x 8 (p+1)^2 CPD^3 bytes of per-step
- * buffers per box. Synchronous.
+ * harmonic, which fixes the rest): 409 of them at p = 8. Each is kept in
+ * Fourier space as a real function, its transform over i^|q| (the tensor has
+ * the parity of its order), about 4 x 409 CPD^3 bytes (3.5 GB at
+ * CPD = 129); about four times that is held while it is built. Per step:
+ * 3 x 8 (p+1)^2 CPD^3 bytes of buffers per box, plus, shared by the boxes,
+ * 16 x p(p+1)(p+2)/6 bytes per cell of the largest box and 4 bytes per
+ * particle of capacity. Synchronous.
  * Returns NF_OK, NF_EINVAL (order, a CPD above 192), NF_ENOMEM or NF_ECUDA
  * (cuFFT errors included).
  */
