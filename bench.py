@@ -3,14 +3,18 @@
 One step = one pass of the whole hot path over the workload: binning (cell
 ids, counts, scan, stable sort, cell-relative records), work-list build,
 pair kernel with per-sink reduction and un-permute, FP64 momentum check.
+Options add the far field of order P to each step (--far P), time a whole
+kick-drift-kick step instead (--kdk), or the forward pass plus the adjoint
+(--workload adjoint).
 Inputs are resident in HBM when the timed region starts (positions of the
 512^3 late-time box are 1.6 GB, larger than L2, so no flush is needed).
 
 Metric: near-field pair interactions per second (whole job), with particle
 updates per second and the fraction of the FP32 CUDA-core peak beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload late|early|tiny|adjoint]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload late|early|tiny|adjoint|batched]
                   [--impl ours|reference] [--precision fp32|fp32_comp|fp64]
+                  [--softening plummer|spline] [--kde] [--far P] [--kdk]
 
 Multi-GPU runs are replicas (one process per GPU, each the same workload;
 the near field of one box is not split across GPUs): value = the units all
@@ -35,7 +39,7 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_PAIR = 20          # Plummer pair: 3 sub, 3 fma, rsqrt (2), 3 mul (r^3, m), 3 fma
 SPLINE_EXTRA_FLOPS = 6       # r = s rsqrt(s), two fma for the polynomial, min
 KDE_EXTRA_FLOPS = 4          # fma for 1 - r^2/b^2, max with 0, add
-VJP_FLOPS_PER_PAIR = 45      # adjoint pair (see the design notes)
+VJP_FLOPS_PER_PAIR = 45      # adjoint pair: D, s, rsqrt, s^-3/2, s^-5/2, u = m_k w_j - m_j w_k, D.u, J u
 SPLINE_VJP_EXTRA_FLOPS = 8   # r = s rsqrt(s), two fma for the polynomial, fma for f'/r, min
 METRIC = "near-field pair interactions/s"
 UNIT = "interactions/s"
