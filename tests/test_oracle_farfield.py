@@ -198,3 +198,23 @@ def test_far_plus_near_equals_ewald_other_radii(cpd, R):
     # the error falls with the separation of the nearest far cells, R + 1:
     # about 3e-5 at R = 1 and 4e-8 at R = 3 (p = 8)
     assert np.median(e) < (1e-4 if R == 1 else 2e-7), np.median(e)
+
+
+def test_far_field_of_a_perfect_lattice_vanishes():
+    """One particle per cell at the same offset from every cell centre: the
+    periodic force on each is zero by symmetry, and so is its near field
+    (every pair is a lattice vector, matched by its opposite), so the far
+    field is zero too, up to the truncation of the series, which falls
+    geometrically with p. A wrong sign on the odd moments, a missing
+    factorial or a lopsided near block leaves a force of the order of the
+    far field of a random box."""
+    cpd, L, R = 5, 1.0, 2
+    g = (np.arange(cpd) + 0.5) / cpd
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    lat = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1) + np.array([0.1, -0.2, 0.3]) / cpd
+    m0 = 1.0 / len(lat)
+    rng = np.random.default_rng(0)
+    scale = np.median(np.linalg.norm(oracle.far_accel(rng.random((len(lat), 3)), L, cpd, R, 6, m0=m0), axis=1))
+    big = [np.abs(oracle.far_accel(lat, L, cpd, R, p, m0=m0)).max() for p in (4, 6, 8)]
+    assert big[2] < 1e-7 * scale, (big, scale)
+    assert big[0] > 10 * big[1] > 100 * big[2], big

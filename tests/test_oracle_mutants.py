@@ -118,6 +118,7 @@ def _run_pins(first_only=False):
         ("vjp_spline_fd", lambda: S.test_spline_vjp_central_differences(oracle)),
         ("far_lattice_constant", lambda: F.test_tensor_origin_value_is_the_cubic_lattice_constant(5)),
         ("far_parity", F.test_tensor_has_the_parity_of_its_order),
+        ("far_lattice", F.test_far_field_of_a_perfect_lattice_vanishes),
         ("far_vs_ewald", F.test_far_plus_near_equals_ewald_and_converges_with_order),
         ("far_cell_shift", F.test_far_field_follows_a_whole_cell_shift),
     ]
