@@ -242,6 +242,10 @@ def run_reference(args):
         return 0
     import oracle
     import synth
+    if world > 1:
+        # a launcher gives every rank one OpenMP thread; the other ranks do no
+        # work here, so rank 0's oracle takes the host's cores
+        oracle.set_num_threads(len(os.sched_getaffinity(0)))
     boxes = synth.batched() if args.workload == "batched" else [make_workload(args.workload)]
     vjp = args.workload == "adjoint"
     prepared = []
