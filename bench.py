@@ -855,7 +855,9 @@ def run_ours(args):
 
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline:
+    # the CPU oracle (baseline and error check) runs at N = 1 only: with more
+    # ranks it would hold every GPU idle while one host works
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         rate, sample, got, ref = run.oracle_check(args.cpu_seconds)
         dn = np.linalg.norm(got - ref, axis=1)
