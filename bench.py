@@ -181,6 +181,27 @@ def make_workload(name: str):
     return synth.make(name)
 
 
+def host_cpu_model(cpuinfo: str = "/proc/cpuinfo") -> str:
+    """The host CPU's model from /proc/cpuinfo ("model name", or the ARM
+    implementer and part codes where there is none), else the machine name."""
+    import platform
+    try:
+        fields = {}
+        with open(cpuinfo) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                fields.setdefault(k.strip(), v.strip())
+        if fields.get("model name"):
+            return fields["model name"]
+        arm_parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2"}
+        if fields.get("CPU part"):
+            part = fields["CPU part"].lower()
+            return f"{platform.machine()} {arm_parts.get(part, 'part ' + part)} (implementer {fields.get('CPU implementer', '?')})"
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
+
+
 def oracle_single_core_tiny():
     """The oracle on one host core over the whole 32^3 tiny box (about 1.8e8
     interactions, a second or two)."""
@@ -303,6 +324,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "cpu_model": host_cpu_model(),
                          "sample": f"{int(np.mean(sizes))} random sinks per step ({'VJP' if vjp else 'accelerations'}) "
                                    f"of the {name} workload"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -871,7 +893,7 @@ def run_ours(args):
                "max_over_rms": float(dn.max() / rms) if rms > 0 else 0.0,
                "tiny_reference_sinks": int(np.sum(rn < 1e-3 * rms))}
         cpu = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": sample, "single_core_tiny": oracle_single_core_tiny()}
+               "sample": sample, "cpu_model": host_cpu_model(), "single_core_tiny": oracle_single_core_tiny()}
 
     tuning = run.tuning()
     cfg = run.config()

@@ -49,3 +49,14 @@ def test_reference_arm_under_a_launcher_prints_once_from_rank_0():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+
+
+def test_host_cpu_model_from_cpuinfo(tmp_path):
+    import bench
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.00GHz\nflags\t: fpu\n")
+    assert bench.host_cpu_model(str(x86)) == "Some CPU @ 2.00GHz"
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n")
+    assert "Neoverse-V2" in bench.host_cpu_model(str(arm))
+    assert bench.host_cpu_model(str(tmp_path / "missing"))
