@@ -3,8 +3,8 @@
  * near/far split (Maksimova et al. 2021, "AbacusSummit", Sec. 3.1).
  *
  * TEST INFRASTRUCTURE ONLY. Nothing in the product library calls, links or
- * includes this file; only the tests use it. It shares no code with the CUDA
- * path.
+ * includes this file; only the tests, the smoke check and the CPU-baseline
+ * leg of the benchmark use it. It shares no code with the CUDA path.
  *
  * What Sec. 3.1 fixes:
  *   - the force on a particle is the near field (the direct sum over the
