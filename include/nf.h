@@ -60,7 +60,7 @@ typedef enum nf_status {
 typedef enum nf_softening {
     NF_SOFT_PLUMMER = 0,    /* Plummer law above (Sec. 5.2) */
     NF_SOFT_SPLINE = 1      /* spline law that is exactly Newtonian for r >= eps
-                               (Sec. 2.4, Sec. 5.2): inside, the pair force is
+                               (Sec. 2.5, Sec. 5.2): inside, the pair force is
                                G m r (10 - 15 u + 6 u^2) / eps^3 with u = r / eps,
                                the lowest-order r P(r/eps) meeting 1/r^2 at eps
                                with continuous first and second derivatives; eps
@@ -241,7 +241,7 @@ NF_API int nf_far_init(nf_ctx *ctx, int order, void *stream);
 NF_API int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream);
 
 /*
- * Particle update with a global timestep (Sec. 2.4: second-order leapfrog,
+ * Particle update with a global timestep (Sec. 2.5: second-order leapfrog,
  * kick-drift-kick). All arrays are device [N x 3] float32 in input order, N
  * and the box of each particle being those of the last nf_bin_particles.
  *

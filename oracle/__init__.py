@@ -153,7 +153,7 @@ LAWS = {"plummer": 0, "spline": 1}
 def accel_ex(pos, L: float, cpd: int, R: int, eps: float, *, law: str = "plummer",
              kde_b: float = 0.0, mass=None, m0: float = 1.0, sinks=None, cid=None):
     """Near-field accelerations with the Plummer law (Sec. 5.2) or the spline
-    law that returns to 1/r^2 at r >= eps (Sec. 2.4, 5.2), and, for kde_b > 0,
+    law that returns to 1/r^2 at r >= eps (Sec. 2.5, 5.2), and, for kde_b > 0,
     the kernel density estimate sum_j m_j (1 - r^2/b^2)_+ (Sec. 3.3).
     Returns acc, or (acc, density) when kde_b > 0."""
     if cid is None:
@@ -212,7 +212,7 @@ def interactions(cid, cpd: int, R: int, per_sink: bool = False):
 
 
 def cell_timestep(vel, acc, cid, cpd: int, eta: float = 0.25) -> float:
-    """Small-scale timestep criterion (Sec. 2.4): eta times the minimum over
+    """Small-scale timestep criterion (Sec. 2.5): eta times the minimum over
     cells of velocity dispersion / maximum particle acceleration."""
     vel = np.ascontiguousarray(vel, dtype=np.float64)
     acc = np.ascontiguousarray(acc, dtype=np.float64)
@@ -236,7 +236,7 @@ def wrap_f32(x, L: float):
 def kdk_step(pos32, vel32, dt: float, L: float, cpd: int, R: int, eps: float, *, m0: float,
              acc0=None, far_order: int = 0):
     """One second-order kick-drift-kick leapfrog step with a global timestep
-    (Sec. 2.4): v += a(x) dt/2; x += v dt (wrapped); v += a(x') dt/2, with the
+    (Sec. 2.5): v += a(x) dt/2; x += v dt (wrapped); v += a(x') dt/2, with the
     near-field accelerations re-binned at x' (plus the far field of order
     ``far_order`` when it is > 0: the total force). Positions and velocities
     are float32 as on the device; the arithmetic is double. Returns

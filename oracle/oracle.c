@@ -210,7 +210,7 @@ int orc_accel(int64_t n, const double *pos, const int32_t *cid, const double *ma
  * orc_accel_ex: the near-field sum of orc_accel with a choice of pair law,
  * plus the kernel density estimate of Sec. 3.3.
  *   law 0 (Plummer, Sec. 5.2): f(r) = (r^2 + eps^2)^(-3/2)
- *   law 1 (spline): the force returns to exactly 1/r^2 at r >= eps (Sec. 2.4,
+ *   law 1 (spline): the force returns to exactly 1/r^2 at r >= eps (Sec. 2.5,
  *       Sec. 5.2 describe such a spline without printing it); inside,
  *       F(r) = r (10 - 15 u + 6 u^2) / eps^3 with u = r / eps, the lowest-order
  *       form r P(u) that meets 1/r^2 at u = 1 with continuous first and second
@@ -427,7 +427,7 @@ int64_t orc_interactions(int64_t n, const int32_t *cid, int cpd, int R, int64_t 
 }
 
 /*
- * orc_cell_timestep: the small-scale timestep criterion of Sec. 2.4, the
+ * orc_cell_timestep: the small-scale timestep criterion of Sec. 2.5, the
  * minimum over cells of (per-cell velocity dispersion) / (per-cell maximum
  * particle acceleration), times eta. The dispersion is the 3-D rms of
  * v - <v>_cell; cells with fewer than two particles or with all

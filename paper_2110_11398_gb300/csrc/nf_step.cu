@@ -1,5 +1,5 @@
 // nf_step.cu -- particle update of the leapfrog integrator with a global
-// timestep (Maksimova et al. 2021, Sec. 2.4): kick, drift (wrapped into the
+// timestep (Maksimova et al. 2021, Sec. 2.5): kick, drift (wrapped into the
 // periodic box), and the small-scale timestep criterion, the minimum over
 // cells of velocity dispersion / maximum particle acceleration times eta.
 #include <cuda_runtime.h>

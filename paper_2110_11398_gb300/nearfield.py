@@ -219,7 +219,7 @@ class NearField:
                                    _stream_ptr(self.device)), self._ctx, "nf_drift")
 
     def timestep(self, vel: torch.Tensor, acc: torch.Tensor, eta: float = 0.25) -> float:
-        """eta * min over cells of velocity dispersion / max |a| (Sec. 2.4)."""
+        """eta * min over cells of velocity dispersion / max |a| (Sec. 2.5)."""
         vel, acc = self._check_vec3(vel, "vel"), self._check_vec3(acc, "acc")
         out = ctypes.c_double()
         N.check(self._lib.nf_timestep(self._ctx, vel.data_ptr(), acc.data_ptr(), float(eta),

@@ -9,10 +9,10 @@ The AbacusSummit particle snapshots are not available, so these recipes stand
 in for them, keeping the shapes the paper describes:
 
 * about 60 particles per cell (the paper's base boxes use CPD=1701 for 6912^3
-  particles, 67 per cell; Sec. 2.4);
+  particles, 67 per cell; Sec. 2.5);
 * Plummer-equivalent softening at 1/40 of the mean interparticle spacing (the
-  paper's 7.2 kpc/h proper for a 2 Gpc/h, 6912^3 box; Sec. 2.4);
-* early times: particles close to a lattice (the initial grid; Sec. 2.3);
+  paper's 7.2 kpc/h proper for a 2 Gpc/h, 6912^3 box; Sec. 2.5);
+* early times: particles close to a lattice (the initial grid; Sec. 2.4);
 * late times: strongly clustered, with most of the pair work inside halos
   (the paper's late-epoch timing is dominated by the near field; Sec. 4.3).
 
