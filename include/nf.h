@@ -65,7 +65,8 @@ typedef enum nf_softening {
                                the lowest-order r P(r/eps) meeting 1/r^2 at eps
                                with continuous first and second derivatives; eps
                                is the radius where the law becomes 1/r^2.
-                               FP32 precision, forward pass only. */
+                               NF_PREC_FP32 contexts only; forward pass,
+                               density estimate and adjoint. */
 } nf_softening;
 
 typedef enum nf_precision {
