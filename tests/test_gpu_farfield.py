@@ -186,3 +186,16 @@ def test_far_field_properties_at_full_early_size(dev):
     d6 = (a6 - a8).double().norm(dim=1) / a8.double().norm(dim=1)
     assert d6.median().item() < 1e-4, d6.median().item()
     nf.close()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 7])
+def test_far_matches_the_oracle_every_order(dev, p):
+    """Every order the library takes (the templated Taylor kernel has one
+    instance per order), on an even CPD."""
+    rng = np.random.default_rng(40 + p)
+    n, L, cpd = 1500, 1.0, 6
+    pos = rng.random((n, 3)).astype(np.float32)
+    got, _ = far_gpu(pos, L, cpd, 1e-3, dev, p=p, gm=1.0 / n)
+    ref = oracle.far_accel(pos.astype(np.float64), L, cpd, 2, p, m0=1.0 / n)
+    e = rel(got, ref)
+    assert np.median(e) < 2e-6 and np.quantile(e, 0.999) < 1e-4, (np.median(e), np.quantile(e, 0.999))
