@@ -13,8 +13,15 @@ Metric: near-field pair interactions per second (whole job), with particle
 updates per second and the fraction of the FP32 CUDA-core peak beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload late|early|tiny|adjoint|batched]
-                  [--impl ours|reference] [--precision fp32|fp32_comp|fp64]
+                  [--impl ours|reference] [--precision fp32|fp32_comp|fp32_comp_pair|fp64]
                   [--softening plummer|spline] [--kde] [--far P] [--kdk]
+
+The default late-workload line also carries, after its own timed region,
+the two other forms on the same GPU: "batched" (64 uneven boxes in one
+persistent launch replayed from a CUDA graph, against the same boxes run as
+sequential single-box contexts) and "adjoint" (forward pass plus the VJP on
+the clustered 128^3 box), each with its fraction of the FP32 peak, its error
+against the FP64 oracle and its own clock record (--no-forms skips them).
 
 Multi-GPU runs are replicas (one process per GPU, each the same workload;
 the near field of one box is not split across GPUs): value = the units all
@@ -42,6 +49,7 @@ KDE_EXTRA_FLOPS = 4          # fma for 1 - r^2/b^2, max with 0, add
 VJP_FLOPS_PER_PAIR = 45      # adjoint pair: D, s, rsqrt, s^-3/2, s^-5/2, u = m_k w_j - m_j w_k, D.u, J u
 SPLINE_VJP_EXTRA_FLOPS = 8   # r = s rsqrt(s), two fma for the polynomial, fma for f'/r, min
 METRIC = "near-field pair interactions/s"
+L2_BYTES = 129e6             # GB300 L2
 UNIT = "interactions/s"
 
 
@@ -98,6 +106,17 @@ def aggregate(local_ms: float, local_units: float, dist=None) -> tuple[float, fl
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(t.item()), float(u.item())
+
+
+# Algorithmic bytes of one binning pass: per particle, read the position
+# (12 B) and its mass (4 B), write the cell-sorted record (16 B) and the
+# permutation (4 B), and re-read the cell id once (4 B); per cell, write the
+# count and the start (8 B).
+BINNING_BYTES_RULE = "40 B/particle (12 pos + 4 mass + 16 record + 4 perm + 4 cell-id re-read) + 8 B/cell"
+
+
+def binning_bytes(n_particles: int, n_cells: int) -> int:
+    return 40 * int(n_particles) + 8 * int(n_cells)
 
 
 def measured_peaks():
@@ -253,6 +272,14 @@ def oracle_sample(box, target_s: float, seed: int = 123):
     return inter / dt, m, inter, dt, idx, acc
 
 
+def workload_keys(interactions: int, max_occ: int, n: int, world: int, batched: bool) -> dict:
+    """Config keys shared by both arms: the work of one step and where it lives."""
+    return {"interactions_per_step": int(interactions), "max_occupancy": int(max_occ),
+            "l2": ("inputs larger than L2 (positions %.2f GB)" if 12 * n > L2_BYTES else
+                   "inputs smaller than L2 (positions %.2f GB), no flush between steps") % (12 * n / 1e9),
+            "parallelism": f"boxes sharded x{world}" if batched else f"replicas x{world}"}
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args):
     """The oracle (FP64 C, OpenMP over sinks) as it stands, on host cores,
@@ -317,6 +344,12 @@ def run_reference(args):
         b0 = boxes[0]
         cfg = {"workload": b0.name, "n": b0.n, "cpd": b0.cpd, "R": b0.R, "eps": b0.eps,
                "softening": "plummer"}
+    # the same workload keys as the measured arm: interactions of one step
+    # (forward, plus the VJP for the adjoint workload) and the fullest cell
+    inter_all = sum(int(p[2].sum()) for p in prepared) * (2 if vjp else 1)
+    max_occ = max(int(np.bincount(p[1]).max()) if len(p[1]) else 0 for p in prepared)
+    cfg.update(workload_keys(inter_all, max_occ, int(sum(b.n for b in boxes)), world,
+                             args.workload == "batched"))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
@@ -736,6 +769,123 @@ class BatchedRunner:
             nf.close()
 
 
+def _error_stats(got, ref):
+    dn = np.linalg.norm(np.asarray(got, np.float64) - ref, axis=1)
+    rn = np.linalg.norm(ref, axis=1)
+    e = dn / np.maximum(rn, 1e-300)
+    return {"median": float(np.median(e)), "p99.9": float(np.quantile(e, 0.999)),
+            "max": float(e.max()), "sinks": int(len(e))}
+
+
+def run_extra_forms(args, dev, sm_count: int, sm_max: float):
+    """The batched and the adjoint forms on the same GPU, after the headline:
+    each timed with CUDA events on the current stream (with its own clock
+    record) and checked against the FP64 oracle on sampled sinks."""
+    import torch
+    import oracle
+    import synth
+    out = {}
+    peak = fp32_peak_tflops(sm_count, sm_max)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    # ---- batched: 64 boxes in one binning and one persistent launch (graph replay)
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.far = "batched", 0
+    t0 = time.perf_counter()
+    run = BatchedRunner(a, dev)
+    gen_s = time.perf_counter() - t0
+    for _ in range(2):
+        run.step()
+    torch.cuda.synchronize()
+    st = run.stats()
+    inter = st["interactions"]
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    steps = args.form_steps
+    pair = []
+
+    def bstep():
+        run.step()
+        pair.append(run.stats()["pair_ms"])
+
+    ms = timed(bstep, steps)
+    run.sequential_step()
+    seq_ms = timed(run.sequential_step, steps)
+    clk = clocks.stop()
+    kern = float(np.mean(pair))
+    # oracle on sampled sinks of every eighth box
+    gots, refs = [], []
+    for bi in range(0, len(run.boxes), 8):
+        b, o0 = run.boxes[bi], int(run.offs[bi])
+        idx = np.sort(np.random.default_rng(b.seed).choice(b.n, 256, replace=False))
+        refs.append(oracle.accel(b.pos, b.L, b.cpd, b.R, b.eps, m0=b.gm, sinks=idx))
+        gots.append(run.out[torch.from_numpy(idx + o0).to(dev)].double().cpu().numpy())
+    out["batched"] = {
+        "workload": run.name, "n": int(run.n), "boxes": len(run.boxes),
+        "value": inter / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+        "interactions_per_step": int(inter),
+        "frac": inter * FLOPS_PER_PAIR / (kern / 1e3) / 1e12 / peak, "kernel_ms": kern,
+        "sequential_ms_per_step": seq_ms, "sequential_value": inter / (seq_ms / 1e3),
+        "batched_speedup": seq_ms / ms, "tuning": run.tuning(),
+        "error_vs_oracle": _error_stats(np.concatenate(gots), np.concatenate(refs)),
+        "error_sample": "256 random sinks in each of boxes 0, 8, ..., 56",
+        "generate_s": gen_s, "clocks": clk}
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+
+    # ---- adjoint: forward pass + VJP on the clustered 128^3 box
+    a = argparse.Namespace(**vars(args))
+    a.workload, a.far, a.kde, a.kdk = "adjoint", 0, False, False
+    run = AdjointRunner(a, dev)
+    for _ in range(3):
+        run.step()
+    torch.cuda.synchronize()
+    inter = run.stats()["interactions"]
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    vjp_ms = []
+
+    def astep():
+        run.step()
+        vjp_ms.append(run.stats()["pair_ms"])
+
+    steps = max(args.form_steps, 5)
+    ms = timed(astep, steps)
+    clk = clocks.stop()
+    fwd = float(np.mean(run.fwd_ms[-steps:]))
+    vjp = float(np.mean(vjp_ms))
+    idx = np.sort(np.random.default_rng(99).choice(run.n, 20000, replace=False))
+    gref = oracle.vjp(run.box.pos, run.w_np, run.box.L, run.box.cpd, run.box.R, run.box.eps,
+                      m0=run.box.gm, sinks=idx)
+    aref = oracle.accel(run.box.pos, run.box.L, run.box.cpd, run.box.R, run.box.eps, m0=run.box.gm,
+                        sinks=idx)
+    ii = torch.from_numpy(idx).to(dev)
+    out["adjoint"] = {
+        "workload": run.name, "n": int(run.n),
+        "value": 2 * inter / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+        "step": "bin, accelerations, VJP of sum_i w_i . a_i",
+        "forward_frac": inter * FLOPS_PER_PAIR / (fwd / 1e3) / 1e12 / peak, "forward_ms": fwd,
+        "vjp_frac": inter * VJP_FLOPS_PER_PAIR / (vjp / 1e3) / 1e12 / peak, "vjp_ms": vjp,
+        "vjp_flops_per_interaction": VJP_FLOPS_PER_PAIR, "vjp_over_forward": vjp / fwd,
+        "error_vs_oracle": _error_stats(run.grad[ii].double().cpu().numpy(), gref),
+        "forward_error_vs_oracle": _error_stats(run.out[ii].double().cpu().numpy(), aref),
+        "error_sample": "VJP and accelerations of 20000 random sinks", "clocks": clk}
+    run.close()
+    del run
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -822,13 +972,10 @@ def run_ours(args):
     if clk.get("sm_mhz"):
         roof["frac_at_observed_clock"] = achieved / peak_fn(props.multi_processor_count, clk["sm_mhz"])
     bin_avg = float(np.mean(bin_ms))
-    # algorithmic bytes of the binning: read positions (12 B), write the
-    # cell-sorted record (16 B) and the permutation (4 B) per particle, plus
-    # the per-cell count and start (8 B per cell)
-    bin_bytes = 32 * run.n + 8 * stats0["n_cells"]
+    bin_bytes = binning_bytes(run.n, stats0["n_cells"])
     roof_bin = {"bound": "hbm", "achieved": bin_bytes / (bin_avg / 1e3) / 1e9,
                 "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s", "bin_ms": bin_avg,
-                "bytes_per_launch": bin_bytes}
+                "bytes_per_launch": bin_bytes, "bytes_rule": BINNING_BYTES_RULE}
     roof_bin["frac"] = roof_bin["achieved"] / roof_bin["peak"]
     extra = {}
     if getattr(run, "far_order", 0):
@@ -898,18 +1045,20 @@ def run_ours(args):
     tuning = run.tuning()
     cfg = run.config()
     run.close()
+    forms = {}
+    if (rank == 0 and world == 1 and args.workload == "late" and not args.no_forms
+            and args.precision == "fp32" and args.softening == "plummer" and not args.kde
+            and not args.far and not args.kdk):
+        forms = run_extra_forms(args, dev, props.multi_processor_count, sm_max)
     if rank == 0:
-        cfg.update({"interactions_per_step": interactions * run.passes,
-                    "max_occupancy": stats0["max_occupancy"], "precision": args.precision,
-                    "tuning": tuning,
-                    "l2": "inputs larger than L2 (positions %.2f GB)" % (12 * run.n / 1e9),
-                    "parallelism": (f"boxes sharded x{world}" if isinstance(run, BatchedRunner)
-                                    else f"replicas x{world}")})
+        cfg.update(workload_keys(interactions * run.passes, stats0["max_occupancy"], run.n, world,
+                                 isinstance(run, BatchedRunner)))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": scaling, "vs_baseline": None, "dtype": "f64" if fp64 else "f32", "data": "synthetic",
             "config": cfg,
+            "precision": args.precision, "tuning": tuning,
             "particle_updates_per_s": updates,
             "fp32_peak_frac": None if fp64 else roof["frac"],
             "roofline": roof, "roofline_binning": roof_bin,
@@ -917,6 +1066,7 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err,
         }
         line.update(extra)
+        line.update(forms)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -930,7 +1080,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="late", choices=["tiny", "early", "late", "adjoint", "batched"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_comp", "fp32_comp_pair", "fp64"])
     ap.add_argument("--softening", default="plummer", choices=["plummer", "spline"])
     ap.add_argument("--kde", action="store_true", help="also compute the kernel density estimate")
     ap.add_argument("--far", type=int, default=0, metavar="P",
@@ -944,6 +1094,10 @@ def main(argv=None):
                     help="oracle seconds per step of the reference arm (default: 2-20 s, sized to the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and adjoint forms that the late workload reports beside it")
+    ap.add_argument("--form-steps", type=int, default=3,
+                    help="timed steps of each of those forms (after their own warm-up)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -12,12 +12,14 @@ namespace nf {
 
 namespace {
 
-// v += a * h, element by element over N x 3, in double with one rounding
-// to float (a float h would carry its own rounding into every update).
+// v += a * h, element by element over N x 3, in double: the product and the
+// sum are each rounded (no fused multiply-add, so the sequence is the plain
+// IEEE one), then the result is rounded once to float (a float h would carry
+// its own rounding into every update).
 __global__ void k_kick(float *__restrict__ vel, const float *__restrict__ acc, int64_t n3, double h) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
          i += (int64_t)gridDim.x * blockDim.x)
-        vel[i] = (float)fma((double)acc[i], h, (double)vel[i]);
+        vel[i] = (float)__dadd_rn((double)vel[i], __dmul_rn((double)acc[i], h));
 }
 
 __device__ __forceinline__ int box_of(const int64_t *poff, int n_boxes, int64_t i) {
@@ -29,8 +31,10 @@ __device__ __forceinline__ int box_of(const int64_t *poff, int n_boxes, int64_t 
     return lo;
 }
 
-// x += v * dt in double, wrapped into [0, L) of the particle's box, rounded
-// once to float; a value that rounds up to L is the periodic image of 0.
+// x += v * dt in double (product and sum each rounded, no fused
+// multiply-add), wrapped into [0, L) of the particle's box by the exact
+// remainder fmod(x, L) plus L when that is negative, rounded once to float;
+// a value that rounds up to L is the periodic image of 0.
 __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, int64_t n,
                         const int64_t *__restrict__ poff, int n_boxes,
                         const BoxDev *__restrict__ boxes, double dt) {
@@ -41,9 +45,11 @@ __global__ void k_drift(float *__restrict__ pos, const float *__restrict__ vel, 
         const float Lf = (float)L;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double x = (double)pos[3 * i + a] + dt * (double)vel[3 * i + a];
-            if (x < 0.0 || x >= L) x -= L * floor(x / L);
-            float f = (float)x;
+            const double x = __dadd_rn((double)pos[3 * i + a], __dmul_rn(dt, (double)vel[3 * i + a]));
+            double r = fmod(x, L);                  // exact
+            if (r < 0.0) r = __dadd_rn(r, L);
+            else if (r == 0.0) r = 0.0;             // -0 becomes +0
+            float f = (float)r;
             if (f >= Lf || f < 0.f) f = 0.f;
             pos[3 * i + a] = f;
         }

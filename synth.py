@@ -22,6 +22,7 @@ folded into a single equal mass 1/N.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -218,19 +219,28 @@ def _scaled_halos(n: int) -> int:
     return max(1, int(round(20000 * n / 512 ** 3)))
 
 
-def batched(n_boxes: int = 64, seed0: int = 3, lo_side: int = 64, hi_side: int = 192) -> list[Box]:
+def batched(n_boxes: int = 64, seed0: int = 3, lo_side: int = 64, hi_side: int = 192,
+            workers: int | None = None) -> list[Box]:
     """Independent clustered boxes with N log-uniform in [lo_side^3, hi_side^3].
 
-    Box b uses seed ``seed0 + b``; CPD_b = round(cbrt(N_b / 60)).
+    Box b uses seed ``seed0 + b``; CPD_b = round(cbrt(N_b / 60)). Boxes are
+    drawn on ``workers`` threads (default: the host's cores, at most 16);
+    each box has its own generator, so the result does not depend on it.
     """
-    boxes = []
-    for b in range(n_boxes):
+    def one(b):
         rng = np.random.default_rng(seed0 + b)
         n = int(round(math.exp(rng.uniform(math.log(lo_side ** 3), math.log(hi_side ** 3)))))
         cpd = max(5, int(round((n / 60.0) ** (1.0 / 3.0))))
         pos, info = clustered_box(n, seed0 + b + 1000, n_halos=_scaled_halos(n))
-        boxes.append(Box(f"batched_box{b}", pos, 1.0, cpd, _eps(n), 1.0 / n, 2, seed0 + b, info))
-    return boxes
+        return Box(f"batched_box{b}", pos, 1.0, cpd, _eps(n), 1.0 / n, 2, seed0 + b, info)
+
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1)
+    if workers <= 1 or n_boxes <= 1:
+        return [one(b) for b in range(n_boxes)]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(one, range(n_boxes)))
 
 
 def adjoint(seed: int = 4, n_side: int = 128, cpd: int = 33) -> Box:

@@ -1,6 +1,6 @@
 """GPU parity for the spline pair law and the in-pass kernel density estimate.
 
-Spline law: exactly Newtonian for r >= eps_s (Maksimova et al. 2021, Sec. 2.4
+Spline law: exactly Newtonian for r >= eps_s (Maksimova et al. 2021, Sec. 2.5
 and Sec. 5.2), r (10 - 15u + 6u^2)/eps_s^3 inside (the reading pinned in
 tests/test_oracle_spline_kde.py). Density: sum_j G m_j (1 - r^2/b^2)_+ over
 the near field, b = 0.4 of the mean spacing (Sec. 3.3). Tolerances as for the

@@ -1,7 +1,7 @@
 """Pins for the oracle's spline force law and kernel density estimate.
 
 Spline law: the near-field force returns to exactly 1/r^2 beyond a finite
-radius (Maksimova et al. 2021, Sec. 2.4 and Sec. 5.2). The reading used here
+radius (Maksimova et al. 2021, Sec. 2.5 and Sec. 5.2). The reading used here
 is the lowest-order law F = r P(r/eps) that meets 1/r^2 at r = eps with
 continuous first and second derivatives. The checks below fix it from the
 outside: 1/r^2 beyond eps, continuity of F, F' and F'' at eps measured from

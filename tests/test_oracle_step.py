@@ -1,5 +1,5 @@
 """Pins for the oracle's particle update: the timestep criterion and the
-kick-drift-kick leapfrog step (Maksimova et al. 2021, Sec. 2.4).
+kick-drift-kick leapfrog step (Maksimova et al. 2021, Sec. 2.5).
 
 The criterion is checked on hand-built cells. The step is checked by
 properties a leapfrog must have: time reversibility, bounded energy error

@@ -8,6 +8,9 @@ shared by all calls, so these checks run it several times in a row with
 different sizes: each call must give exactly the cell table, permutation and
 cell-relative records of nf_bin_particles + nf_copy_binning (binning is exact
 work, so the comparison is bit for bit, as in the other binning tests).
+The limits are run at their edge (2^20 particles, CPD 64), together with an
+empty input, an out-of-range position, and a check that repeated calls leave
+the device's free memory unchanged.
 This file is collected last so that a failure here stops a -x run only after
 every other test has run.
 """
@@ -97,3 +100,74 @@ def test_noalloc_rejects_sizes_beyond_its_limit(env):
     rc = lib.nf_bin_cells_noalloc(pos.data_ptr(), None, 1.0, 16, 1.0, 65, cs.data_ptr(),
                                   cs.data_ptr(), buf.data_ptr(), None)
     assert rc == -1 and b"cpd" in lib.nf_last_error(None)
+
+
+def test_noalloc_at_its_particle_limit(env):
+    """n = 2^20 particles at CPD = 64 (the largest sizes the static array is
+    cut for), bit for bit against the allocating binning."""
+    lib, dev = env
+    rng = np.random.default_rng(12)
+    n = 1 << 20
+    halo = (np.array([0.3, 0.6, 0.2]) + 0.01 * rng.standard_normal((n // 4, 3))) % 1.0
+    pos = np.concatenate([rng.random((n - n // 4, 3)), halo]).astype(np.float32)
+    pos[pos >= np.float32(1.0)] = 0
+    p = torch.from_numpy(pos).to(dev)
+    got = _noalloc(lib, dev, p, 1.0, 64, 1.0 / n)
+    ref = _allocating(dev, p, 1.0, 64, 1.0 / n)
+    assert np.array_equal(got[0], ref[0])
+    assert np.array_equal(got[1], ref[1])
+    assert np.array_equal(got[2].view(np.uint32), ref[2].view(np.uint32))
+
+
+def test_noalloc_empty_input(env):
+    lib, dev = env
+    cpd = 7
+    cs = torch.full((cpd ** 3 + 1,), -7, dtype=torch.int32, device=dev)
+    rc = lib.nf_bin_cells_noalloc(None, None, 1.0, 0, 1.0, cpd, cs.data_ptr(), None, None,
+                                  torch.cuda.current_stream(dev).cuda_stream)
+    assert rc == 0, lib.nf_last_error(None)
+    assert np.all(cs.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("bad", [1.0, float("nan"), -1e-3])
+def test_noalloc_out_of_range_position(env, bad):
+    lib, dev = env
+    pos = np.random.default_rng(3).random((4000, 3)).astype(np.float32)
+    pos[123, 1] = bad
+    p = torch.from_numpy(pos).to(dev)
+    cs = torch.empty(9 ** 3 + 1, dtype=torch.int32, device=dev)
+    perm = torch.empty(4000, dtype=torch.int32, device=dev)
+    srt = torch.empty((4000, 4), dtype=torch.float32, device=dev)
+    rc = lib.nf_bin_cells_noalloc(p.data_ptr(), None, 1.0, 4000, 1.0, 9, cs.data_ptr(), perm.data_ptr(),
+                                  srt.data_ptr(), torch.cuda.current_stream(dev).cuda_stream)
+    assert rc == -2 and b"outside" in lib.nf_last_error(None)
+    # the shared array is usable again at once
+    ok = _noalloc(lib, dev, torch.from_numpy(np.random.default_rng(4).random((4000, 3)).astype(np.float32)).to(dev),
+                  1.0, 9, 1.0)
+    assert ok[0][-1] == 4000
+
+
+def test_noalloc_calls_leave_free_device_memory_unchanged(env):
+    """After a first call (which loads the kernels it launches), further calls
+    must not change the device's free memory (cudaMemGetInfo)."""
+    lib, dev = env
+    pos, L, cpd, gm, mass = _cases(dev)[0]
+    n = pos.shape[0]
+    cs = torch.empty(cpd ** 3 + 1, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    srt = torch.empty((n, 4), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+
+    def call():
+        rc = lib.nf_bin_cells_noalloc(pos.data_ptr(), None, float(gm), n, float(L), cpd, cs.data_ptr(),
+                                      perm.data_ptr(), srt.data_ptr(), stream)
+        assert rc == 0, lib.nf_last_error(None)
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    call()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    call()
+    free2, _ = torch.cuda.mem_get_info(dev)
+    assert free0 == free1 == free2, (free0, free1, free2)
