@@ -13,6 +13,7 @@ Metric: near-field pair interactions per second (whole job), with particle
 updates per second and the fraction of the FP32 CUDA-core peak beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload late|early|tiny|adjoint|batched]
+                  [--decomp replicas|slab]
                   [--impl ours|reference] [--precision fp32|fp32_comp|fp32_comp_pair|fp64]
                   [--softening plummer|spline] [--kde] [--far P] [--kdk]
 
@@ -23,9 +24,12 @@ sequential single-box contexts) and "adjoint" (forward pass plus the VJP on
 the clustered 128^3 box), each with its fraction of the FP32 peak, its error
 against the FP64 oracle and its own clock record (--no-forms skips them).
 
-Multi-GPU runs are replicas (one process per GPU, each the same workload;
-the near field of one box is not split across GPUs): value = the units all
-ranks processed / the max over ranks of the timed region.
+Multi-GPU runs are replicas by default (one process per GPU, each the same
+workload): value = the units all ranks processed / the max over ranks of the
+timed region. --decomp slab instead splits one box into x slabs over the
+ranks (Sec. 3.2), each rank's ghost slabs swapped with its ring neighbours
+before its pair pass; with one rank it measures the same path on its own
+boundary slabs.
 """
 from __future__ import annotations
 
@@ -777,6 +781,95 @@ def _error_stats(got, ref):
             "max": float(e.max()), "sinks": int(len(e))}
 
 
+class SlabRunner:
+    """One box split into x slabs over the ranks (one slab context per rank,
+    ghost slabs swapped with the ring neighbours before the pair pass; with
+    one rank, its own boundary slabs). Step = bin the owned particles, swap
+    and import the ghosts, accelerations of the owned particles."""
+
+    kernel = "k_pairs"
+    flops_per_pair = FLOPS_PER_PAIR
+    e2e_note = "H2D owned positions, bin, ghost swap, accelerations, D2H owned accelerations"
+
+    def __init__(self, args, dev, rank=0, world=1):
+        import torch
+        from paper_2110_11398_gb300.slab import SlabNearField, owners, slab_capacity, slab_of, slab_ranges
+        self.torch = torch
+        self.box = box = make_workload(args.workload)
+        self.name = box.name
+        self.ranges = slab_ranges(box.cpd, world, box.R)
+        x0, nx = self.ranges[rank]
+        pos_all = torch.from_numpy(box.pos).to(dev)
+        own = owners(pos_all, box.L, box.cpd, self.ranges)
+        cap = slab_capacity(slab_of(pos_all, box.L, box.cpd), x0, nx, box.R, box.cpd)
+        self.idx = torch.nonzero(own == rank).squeeze(1)
+        self.pos = pos_all[self.idx].contiguous()
+        del pos_all, own
+        self.n = int(self.pos.shape[0])
+        self.n_total = box.n
+        self.out = torch.empty((self.n, 3), dtype=torch.float32, device=dev)
+        self.sf = SlabNearField(box.L, box.cpd, box.eps, x0, nx, radius=box.R, precision=args.precision,
+                                capacity=cap, device=dev)
+        self.slabs = (x0, nx)
+        self.passes = 1
+        self.law = "plummer"
+        self.kde_b = None
+        self.far_order = 0
+
+    def step(self):
+        from paper_2110_11398_gb300.slab import exchange_and_import
+        self.sf.bin(self.pos, gm=self.box.gm)
+        exchange_and_import(self.sf)
+        self.sf.accel(out=self.out)
+
+    def stats(self):
+        return self.sf.stats()
+
+    def config(self):
+        b = self.box
+        return {"workload": b.name, "n": b.n, "cpd": b.cpd, "R": b.R, "eps": b.eps, "softening": "plummer",
+                "decomposition": f"x slabs {self.ranges}"}
+
+    def e2e(self, reps):
+        torch = self.torch
+        hp = self.pos.cpu().pin_memory()
+        ha = torch.empty((self.n, 3), dtype=torch.float32).pin_memory()
+        pos = torch.empty_like(self.pos)
+
+        def once():
+            pos.copy_(hp, non_blocking=True)
+            from paper_2110_11398_gb300.slab import exchange_and_import
+            self.sf.bin(pos, gm=self.box.gm)
+            exchange_and_import(self.sf)
+            self.sf.accel(out=self.out)
+            ha.copy_(self.out, non_blocking=True)
+            torch.cuda.synchronize()
+
+        once()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            once()
+        return (time.perf_counter() - t0) / reps, int(hp.nbytes), int(ha.nbytes)
+
+    def oracle_check(self, seconds):
+        rate, m, inter_s, dt, idx, ref = oracle_sample(self.box, seconds)
+        # the sampled sinks that this rank owns, in its own order
+        inv = np.full(self.n_total, -1, np.int64)
+        inv[self.idx.cpu().numpy()] = np.arange(self.n)
+        loc = inv[idx]
+        keep = loc >= 0
+        got = self.out[self.torch.from_numpy(loc[keep]).to(self.out.device)].double().cpu().numpy()
+        sample = (f"{int(keep.sum())} random sinks ({inter_s:.3e} interactions timed, {dt:.1f} s) of the "
+                  f"{self.n_total}-particle {self.name} box")
+        return rate, sample, got, ref[keep]
+
+    def tuning(self):
+        return self.sf.tuning
+
+    def close(self):
+        self.sf.close()
+
+
 def run_extra_forms(args, dev, sm_count: int, sm_max: float):
     """The batched and the adjoint forms on the same GPU, after the headline:
     each timed with CUDA events on the current stream (with its own clock
@@ -829,8 +922,21 @@ def run_extra_forms(args, dev, sm_count: int, sm_max: float):
         idx = np.sort(np.random.default_rng(b.seed).choice(b.n, 256, replace=False))
         refs.append(oracle.accel(b.pos, b.L, b.cpd, b.R, b.eps, m0=b.gm, sinks=idx))
         gots.append(run.out[torch.from_numpy(idx + o0).to(dev)].double().cpu().numpy())
+    # the autotuner on three single boxes (smallest, median, largest): the
+    # launch shape (sinks per lane, warps, source tile) that won at each size
+    order = sorted(range(len(run.boxes)), key=lambda i: run.boxes[i].n)
+    tuned = []
+    for bi in (order[0], order[len(order) // 2], order[-1]):
+        b, nf = run.boxes[bi], run.singles[bi]
+        o0, o1 = int(run.offs[bi]), int(run.offs[bi + 1])
+        nf.bin(run.pos[o0:o1], gm=b.gm)
+        t0 = time.perf_counter()
+        shape = nf.autotune(reps=2)
+        tuned.append({"box": bi, "n": int(b.n), "cpd": int(b.cpd), "shape": shape,
+                      "search_s": time.perf_counter() - t0})
     out["batched"] = {
         "workload": run.name, "n": int(run.n), "boxes": len(run.boxes),
+        "autotuned_single_boxes": tuned,
         "value": inter / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
         "interactions_per_step": int(inter),
         "frac": inter * FLOPS_PER_PAIR / (kern / 1e3) / 1e12 / peak, "kernel_ms": kern,
@@ -901,7 +1007,14 @@ def run_ours(args):
 
     if args.far and args.workload == "adjoint":
         raise SystemExit("--far goes with the force workloads (tiny, early, late, batched), not the adjoint")
-    if args.workload == "batched":
+    if args.decomp == "slab":
+        if args.workload not in ("tiny", "early", "late") or args.far or args.kdk or args.kde \
+                or args.softening != "plummer" or args.precision == "fp64":
+            raise SystemExit("--decomp slab goes with the plain one-box force workloads (tiny, early, late), "
+                             "Plummer law, FP32 precisions")
+        run = SlabRunner(args, dev, rank, world)
+        scaling = "strong"
+    elif args.workload == "batched":
         run = BatchedRunner(args, dev, rank, world)
         scaling = "strong"
     elif args.workload == "adjoint":
@@ -1046,13 +1159,18 @@ def run_ours(args):
     cfg = run.config()
     run.close()
     forms = {}
-    if (rank == 0 and world == 1 and args.workload == "late" and not args.no_forms
+    if (rank == 0 and world == 1 and args.workload == "late" and not args.no_forms and args.decomp == "replicas"
             and args.precision == "fp32" and args.softening == "plummer" and not args.kde
             and not args.far and not args.kdk):
         forms = run_extra_forms(args, dev, props.multi_processor_count, sm_max)
     if rank == 0:
-        cfg.update(workload_keys(interactions * run.passes, stats0["max_occupancy"], run.n, world,
-                                 isinstance(run, BatchedRunner)))
+        if isinstance(run, SlabRunner):        # the whole box's work, summed over the slabs
+            _, inter_all = aggregate(0.0, interactions * run.passes, dist_or_none)
+            cfg.update(workload_keys(int(inter_all), stats0["max_occupancy"], run.n_total, world, False))
+            cfg["parallelism"] = f"x slabs x{world}"
+        else:
+            cfg.update(workload_keys(interactions * run.passes, stats0["max_occupancy"], run.n, world,
+                                     isinstance(run, BatchedRunner)))
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -1094,6 +1212,9 @@ def main(argv=None):
                     help="oracle seconds per step of the reference arm (default: 2-20 s, sized to the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="slab: split one box into x slabs over the ranks, ghost slabs swapped between "
+                         "neighbours (with one rank, its own); replicas: every rank runs the whole workload")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched and adjoint forms that the late workload reports beside it")
     ap.add_argument("--form-steps", type=int, default=3,

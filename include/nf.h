@@ -54,7 +54,8 @@ typedef enum nf_status {
     NF_ENOMEM = -3,    /* device or host allocation failed */
     NF_ECUDA = -4,     /* a CUDA runtime call failed; see nf_last_error */
     NF_ESTATE = -5,    /* call out of order (e.g. compute before binning) */
-    NF_ETIMEOUT = -6   /* reserved: no kernel in this library spin-waits */
+    NF_ETIMEOUT = -6   /* a bounded device-side wait gave up (the cell sort's
+                          look-back); the result of that call is invalid */
 } nf_status;
 
 typedef enum nf_softening {
@@ -70,9 +71,14 @@ typedef enum nf_softening {
 } nf_softening;
 
 typedef enum nf_precision {
-    NF_PREC_FP32 = 0,       /* FP32 pair arithmetic on cell-relative coordinates */
-    NF_PREC_FP32_COMP = 1,  /* same, per-sink sums kept as compensated (TwoSum) pairs */
-    NF_PREC_FP64_REF = 2    /* FP64 pair arithmetic on the GPU (reference timing) */
+    NF_PREC_FP32 = 0,       /* FP32 pair arithmetic on cell-relative coordinates;
+                               each 128-source tile is summed afresh and the
+                               tile sums are added to the per-sink total */
+    NF_PREC_FP32_COMP = 1,  /* same pair loop; the tile sums are folded into a
+                               compensated (hi, lo) per-sink total by TwoSum */
+    NF_PREC_FP64_REF = 2,   /* FP64 pair arithmetic on the GPU (reference timing) */
+    NF_PREC_FP32_COMP_PAIR = 3  /* FP32, every pair term added to a compensated
+                                   (hi, lo) total by TwoSum (slowest FP32 form) */
 } nf_precision;
 
 /* Figures of the last binning / compute on a context (see nf_get_stats). */
@@ -95,13 +101,17 @@ typedef struct nf_stats {
 
 /* Launch shape of the pair kernels. sinks_per_lane in {1,2,4}; warps_per_block
  * in {2,4,8,16}; blocks_per_sm = 0 picks the occupancy maximum; use_graph = 1
- * replays the compute phase from a captured CUDA graph. */
+ * replays the compute phase from a captured CUDA graph; source_tile in
+ * {0, 64, 128, 256}: sources staged in shared memory per tile by the plain
+ * (Plummer, no density) FP32 kernels, 0 meaning 128 (the other kernels
+ * always stage 128). */
 typedef struct nf_tuning {
     int sinks_per_lane;
     int warps_per_block;
     int blocks_per_sm;
     int use_graph;
     int vjp_sinks_per_lane;   /* sinks per lane of the adjoint kernel; 0 = as sinks_per_lane */
+    int source_tile;
 } nf_tuning;
 
 /*
@@ -135,7 +145,9 @@ NF_API int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size
  *   stream       cudaStream_t
  * Synchronises `stream` once at the end to report NF_ERANGE for an invalid
  * position (such particles are binned to a safe cell and the context is
- * marked unbinned). Returns NF_OK, NF_EINVAL, NF_ERANGE, NF_ESTATE or NF_ECUDA.
+ * marked unbinned). Returns NF_OK, NF_EINVAL, NF_ERANGE, NF_ETIMEOUT (a
+ * look-back wait of the sort gave up; nothing is binned), NF_ESTATE or
+ * NF_ECUDA.
  */
 NF_API int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double mass_if_null,
                      int64_t n, const int64_t *box_offsets, void *stream);
@@ -246,10 +258,12 @@ NF_API int nf_compute_far(nf_ctx *ctx, float *acc, int accumulate, void *stream)
  * kick-drift-kick). All arrays are device [N x 3] float32 in input order, N
  * and the box of each particle being those of the last nf_bin_particles.
  *
- * nf_kick  -- v += a dt, in double and rounded once to float32.
- * nf_drift -- x += v dt in double, wrapped into [0, L) of the particle's box
- *             and rounded once to float32 (a value that rounds up to L
- *             becomes 0, its periodic image).
+ * nf_kick  -- v += a dt in double (the product and the sum each rounded,
+ *             no fused multiply-add), then rounded once to float32.
+ * nf_drift -- x += v dt in double (likewise unfused), wrapped into [0, L) of
+ *             the particle's box by the exact remainder fmod(x, L) (plus L
+ *             when negative), and rounded once to float32 (a value that
+ *             rounds up to L becomes 0, its periodic image).
  * nf_timestep -- the small-scale criterion: eta times the minimum over cells
  *             of (3-D velocity dispersion about the cell mean) / (maximum
  *             particle |a| in the cell); cells with fewer than two particles
@@ -310,11 +324,74 @@ NF_API int nf_get_tuning(const nf_ctx *ctx, nf_tuning *t);
 
 /*
  * nf_autotune -- time every candidate launch shape of the pair kernel on the
- * currently binned particles (CUDA events on `stream`, `reps` launches each),
- * keep the fastest in the context and copy it to *best (may be NULL).
- * Synchronises `stream`. Requires a prior nf_bin_particles.
+ * currently binned particles (CUDA events on `stream`, `reps` launches each):
+ * sinks_per_lane in {1,2,4} x warps_per_block in {4,8} x source_tile in
+ * {64,128,256} (the tile only where the kernel takes it). Keeps the fastest
+ * in the context and copies it to *best (may be NULL). Synchronises
+ * `stream`. Requires a prior nf_bin_particles.
  */
 NF_API int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream);
+
+/*
+ * Slab decomposition (Sec. 3.2: the box is split into x slabs, a node owns a
+ * contiguous range of them, and a node's near field needs the R slabs on
+ * either side of its range; Sec. 3.1: the near-field radius R sets that
+ * width). A slab context holds one rank's owned slabs and R ghost slabs on
+ * each side. Its accelerations equal, bit for bit, those of a whole-box
+ * context for the same particles (same cells, same source order per cell).
+ *
+ * nf_init_slab -- a context for the owned x slabs [x_begin, x_begin +
+ *   x_count) of one periodic box (other arguments as nf_init).
+ *   x_begin    0 <= x_begin < cpd (global slab index)
+ *   x_count    R <= x_count <= cpd; every rank must own at least R slabs
+ *   precision  NF_PREC_FP32, NF_PREC_FP32_COMP or NF_PREC_FP32_COMP_PAIR
+ *   capacity   largest owned + ghost particle count
+ * nf_bin_particles then takes the OWNED particles only (a particle outside
+ * the owned slabs is NF_ERANGE), and a compute call needs the ghosts of that
+ * binning imported first (else NF_ESTATE). The adjoint, the far field,
+ * nf_kdk_step and nf_accel_host are not available on slab contexts
+ * (NF_EINVAL); nf_kick, nf_drift, nf_timestep (owned cells) and the density
+ * estimate are.
+ *
+ * nf_slab_export -- the R boundary slabs a neighbour needs as ghosts, from
+ *   the last binning: side 0 the first R owned slabs (for the rank on the
+ *   left, whose right ghosts they are), side 1 the last R (for the rank on
+ *   the right). Synchronises `stream` once to read the record count.
+ *   counts     device [R * cpd * cpd] int32 out, or NULL: particles per cell
+ *              of those slabs, cell order (x, y, z), x slowest
+ *   records    device [records_cap x 4] float32 out, or NULL: their
+ *              cell-sorted records (rx, ry, rz, G m), as nf_copy_binning
+ *   n_records  host out: number of records of those slabs
+ *   Returns NF_OK, NF_EINVAL (not a slab context, side, records_cap below
+ *   n_records), NF_ESTATE (not binned) or NF_ECUDA.
+ *
+ * nf_slab_import -- install the ghost slabs for the current binning: the
+ *   left neighbour's side-1 export as left ghosts and the right neighbour's
+ *   side-0 export as right ghosts (with one rank, its own exports). The
+ *   records are copied behind the owned ones and the cell table is rebuilt.
+ *   Synchronises `stream` to check that every ghost count is >= 0 and that
+ *   each side's counts add up to its n.
+ *   left_counts, right_counts    device [R * cpd * cpd] int32
+ *   left_records, right_records  device [n_left x 4], [n_right x 4] float32
+ *   Returns NF_OK, NF_EINVAL (sizes, counts, capacity), NF_ESTATE or NF_ECUDA.
+ *
+ * nf_slab_of -- the global x slab floor((x * cpd) / L) (the binning's own
+ *   arithmetic, Sec. 3.1) of each of n particles, -1 for an x outside [0, L)
+ *   or not finite, on the current device; for routing particles to the rank
+ *   that owns their slab.
+ *   pos   device [n x 3] float32;  slab  device [n] int32 out
+ *   Returns NF_OK, NF_EINVAL or NF_ECUDA (message via nf_last_error(NULL)).
+ *   Asynchronous.
+ */
+NF_API int nf_init_slab(nf_ctx **out, int device, double box_size, int cpd, int radius, double eps,
+                        int softening, int precision, int64_t capacity, int x_begin, int x_count);
+NF_API int nf_slab_export(nf_ctx *ctx, int side, int32_t *counts, float *records, int64_t records_cap,
+                          int64_t *n_records, void *stream);
+NF_API int nf_slab_import(nf_ctx *ctx, const int32_t *left_counts, const float *left_records,
+                          int64_t n_left, const int32_t *right_counts, const float *right_records,
+                          int64_t n_right, void *stream);
+NF_API int nf_slab_of(const float *pos, int64_t n, double box_size, int cpd, int32_t *slab,
+                      void *stream);
 
 /*
  * nf_bin_cells_noalloc -- the binning of nf_bin_particles for one box, for
@@ -337,11 +414,15 @@ NF_API int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream);
  *                (rx, ry, rz, G m) in cell units (as nf_copy_binning)
  * Runs on the current CUDA device and synchronises `stream` before
  * returning (to report NF_ERANGE). The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture. All calls on a device share the one
- * array, which keeps the last call's contents: calls that overlap on the GPU
- * (different streams or threads) race and must be serialised by the caller.
- * Errors: NF_EINVAL, NF_ERANGE, NF_ECUDA; message via nf_last_error(NULL).
+ * array's device address (cudaGetSymbolAddress) and caches it for the life
+ * of the process; make that first call before any stream capture, and do not
+ * reset the device (cudaDeviceReset) between calls, which would move the
+ * array and leave the cached address stale. All calls on a device share the
+ * one array, which keeps the last call's contents: calls that overlap on the
+ * GPU (different streams or threads) race and must be serialised by the
+ * caller.
+ * Errors: NF_EINVAL, NF_ERANGE, NF_ETIMEOUT, NF_ECUDA; message via
+ * nf_last_error(NULL).
  */
 NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, double mass_if_null,
                                 int64_t n, double box_size, int cpd, int32_t *cell_start,

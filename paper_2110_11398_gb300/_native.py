@@ -15,15 +15,17 @@ LIB_PATH = os.path.join(HERE, "_build", "libnf.so")
 NF_OK, NF_EINVAL, NF_ERANGE, NF_ENOMEM, NF_ECUDA, NF_ESTATE, NF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 NF_SOFT_PLUMMER, NF_SOFT_SPLINE = 0, 1
 SOFTENINGS = {"plummer": NF_SOFT_PLUMMER, "spline": NF_SOFT_SPLINE}
-NF_PREC_FP32, NF_PREC_FP32_COMP, NF_PREC_FP64_REF = 0, 1, 2
-PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_PREC_FP64_REF}
+NF_PREC_FP32, NF_PREC_FP32_COMP, NF_PREC_FP64_REF, NF_PREC_FP32_COMP_PAIR = 0, 1, 2, 3
+PRECISIONS = {"fp32": NF_PREC_FP32, "fp32_comp": NF_PREC_FP32_COMP, "fp64": NF_PREC_FP64_REF,
+              "fp32_comp_pair": NF_PREC_FP32_COMP_PAIR}
 
 # every entry point include/nf.h declares
 EXPORTS = ("nf_init", "nf_bin_particles", "nf_compute_accel", "nf_compute_accel_f64",
            "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
            "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
            "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift", "nf_timestep",
-           "nf_kdk_step", "nf_far_init", "nf_compute_far",
+           "nf_kdk_step", "nf_far_init", "nf_compute_far", "nf_init_slab", "nf_slab_export",
+           "nf_slab_import", "nf_slab_of",
            "nf_last_error", "nf_status_string", "nf_free")
 
 
@@ -39,7 +41,7 @@ class nf_stats(ctypes.Structure):
 class nf_tuning(ctypes.Structure):
     _fields_ = [("sinks_per_lane", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("vjp_sinks_per_lane", ctypes.c_int)]
+                ("vjp_sinks_per_lane", ctypes.c_int), ("source_tile", ctypes.c_int)]
 
 
 class NFError(RuntimeError):
@@ -92,6 +94,10 @@ def load(path: str | None = None):
         lib.nf_autotune.argtypes = [vp, i32, P(nf_tuning), vp]
         lib.nf_copy_binning.argtypes = [vp, vp, vp, vp, vp]
         lib.nf_bin_cells_noalloc.argtypes = [vp, vp, dbl, i64, dbl, i32, vp, vp, vp, vp]
+        lib.nf_init_slab.argtypes = [P(vp), i32, dbl, i32, i32, dbl, i32, i32, i64, i32, i32]
+        lib.nf_slab_export.argtypes = [vp, i32, vp, vp, i64, P(i64), vp]
+        lib.nf_slab_import.argtypes = [vp, vp, vp, i64, vp, vp, i64, vp]
+        lib.nf_slab_of.argtypes = [vp, i64, dbl, i32, vp, vp]
         lib.nf_last_error.argtypes = [vp]
         lib.nf_last_error.restype = ctypes.c_char_p
         lib.nf_status_string.argtypes = [i32]
@@ -102,7 +108,8 @@ def load(path: str | None = None):
                      "nf_compute_accel_vjp", "nf_accel_host", "nf_get_stats", "nf_set_tuning",
                      "nf_get_tuning", "nf_autotune", "nf_copy_binning", "nf_bin_cells_noalloc",
                      "nf_far_init", "nf_compute_far", "nf_compute_accel_density", "nf_set_box_masses", "nf_kick", "nf_drift",
-                     "nf_timestep", "nf_kdk_step"):
+                     "nf_timestep", "nf_kdk_step", "nf_init_slab", "nf_slab_export", "nf_slab_import",
+                     "nf_slab_of"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib

@@ -59,7 +59,7 @@ void release(Ctx *c) {
     cudaGetDevice(&prev);
     cudaSetDevice(c->device);
     void *bufs[] = {c->boxes_d, c->poff_d, c->keys_a, c->keys_b, c->vals_a, c->vals_b,
-                    c->count, c->cell_start, c->scan_tmp, c->radix_hist, c->sorted,
+                    c->count, c->cell_start, c->scan_tmp, c->sort_status, c->bin_state, c->sorted,
                     c->sorted_d, c->w_sorted, c->nsrc_cell, c->items, c->decomp_d,
                     c->state, c->mom_partial, c->mom_result, c->st_pos, c->st_mass, c->st_acc,
                     c->step_bits};
@@ -68,9 +68,14 @@ void release(Ctx *c) {
     if (c->state_h) cudaFreeHost(c->state_h);
     if (c->mom_h) cudaFreeHost(c->mom_h);
     if (c->step_bits_h) cudaFreeHost(c->step_bits_h);
+    if (c->pin_i32) cudaFreeHost(c->pin_i32);
     if (c->g_fwd.exec) cudaGraphExecDestroy(c->g_fwd.exec);
     if (c->g_vjp.exec) cudaGraphExecDestroy(c->g_vjp.exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaStream_t cs : c->cp_streams)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : c->cp_events)
+        if (ev) cudaEventDestroy(ev);
     far_release(c);
     cudaEvent_t evs[] = {c->ev_bin0, c->ev_bin1, c->ev_pair0, c->ev_pair1,
                          c->ev_far[0], c->ev_far[1], c->ev_far[2], c->ev_far[3]};
@@ -94,9 +99,10 @@ struct DeviceGuard {
 };
 
 bool valid_tuning(const nf_tuning &t) {
-    const int k = t.sinks_per_lane, w = t.warps_per_block, kv = t.vjp_sinks_per_lane;
+    const int k = t.sinks_per_lane, w = t.warps_per_block, kv = t.vjp_sinks_per_lane, st = t.source_tile;
     return (k == 1 || k == 2 || k == 4) && (w == 2 || w == 4 || w == 8 || w == 16) &&
-           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32 && (kv == 0 || kv == 1 || kv == 2 || kv == 4);
+           t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32 && (kv == 0 || kv == 1 || kv == 2 || kv == 4) &&
+           (st == 0 || st == 64 || st == 128 || st == 256);
 }
 
 int decomp_slot(int K) { return K == 1 ? 0 : (K == 2 ? 1 : 2); }
@@ -132,6 +138,35 @@ cudaError_t record_timing(cudaEvent_t ev, cudaStream_t s) {
     if (e) return e;
     if (cs == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
     return cudaEventRecord(ev, s);
+}
+
+// One host<->device copy of `bytes`, split into four parts on the context's
+// copy streams (each part can take its own copy engine), ordered after the
+// work already on `s` and before the work enqueued on `s` next.
+cudaError_t split_copy(Ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                       cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (!c->cp_streams[0]) {
+        for (cudaStream_t &cs : c->cp_streams)
+            if (!e) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (cudaEvent_t &ev : c->cp_events)
+            if (!e) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e) return e;
+    }
+    if ((e = cudaEventRecord(c->cp_events[4], s))) return e;
+    const size_t part = ((bytes / 4) + 255) & ~size_t(255);
+    for (int i = 0; i < 4; ++i) {
+        const size_t off = part * i;
+        const size_t len = off >= bytes ? 0 : std::min(part, bytes - off);
+        if ((e = cudaStreamWaitEvent(c->cp_streams[i], c->cp_events[4], 0))) return e;
+        if (len && (e = cudaMemcpyAsync(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off,
+                                        len, kind, c->cp_streams[i])))
+            return e;
+        if ((e = cudaEventRecord(c->cp_events[i], c->cp_streams[i]))) return e;
+    }
+    for (int i = 0; i < 4; ++i)
+        if ((e = cudaStreamWaitEvent(s, c->cp_events[i], 0))) return e;
+    return cudaSuccess;
 }
 
 // The compute phase: work list, pair kernel, momentum diagnostic and the
@@ -200,6 +235,8 @@ cudaError_t run_graph(Ctx *c, nf::GraphSlot &slot, const std::vector<uint64_t> &
 
 int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nullptr) {
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel: no binned particles (call nf_bin_particles first)");
+    if (c->slab && !c->ghosts_ready)
+        return fail(c, NF_ESTATE, "nf_compute_accel: slab context without ghosts (call nf_slab_import after binning)");
     if (!acc && c->n > 0) return fail(c, NF_EINVAL, "nf_compute_accel: acc is NULL");
     int rc = ensure_decomp(c, c->precision == NF_PREC_FP64_REF ? 1 : c->tune.sinks_per_lane, s);
     if (rc) return rc;
@@ -208,7 +245,8 @@ int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nu
         std::vector<uint64_t> key = {(uint64_t)(uintptr_t)acc, (uint64_t)f64, (uint64_t)c->n,
                                      (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
                                      (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
-                                     (uint64_t)c->equal_mass, (uint64_t)(uintptr_t)dens};
+                                     (uint64_t)c->equal_mass, (uint64_t)(uintptr_t)dens,
+                                     (uint64_t)c->tune.source_tile};
         e = run_graph(c, c->g_fwd, key,
                       [&](cudaStream_t cs) { return enqueue_forward(c, acc, f64, cs, dens); }, s);
     } else {
@@ -248,8 +286,15 @@ const char *nf_last_error(const nf_ctx *ctx) {
     return reinterpret_cast<const Ctx *>(ctx)->err.c_str();
 }
 
-int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const int *cpd,
-            int radius, const double *eps, int softening, int precision, int64_t capacity) {
+}  // extern "C"
+
+namespace {
+
+// Context creation for nf_init (slab_nx = 0) and nf_init_slab (one box,
+// owned x slabs [slab_x0, slab_x0 + slab_nx) plus R ghost slabs a side).
+int init_impl(nf_ctx **out, int device, int n_boxes, const double *box_size, const int *cpd,
+              int radius, const double *eps, int softening, int precision, int64_t capacity,
+              int slab_x0, int slab_nx) {
     if (!out) return fail(nullptr, NF_EINVAL, "nf_init: out is NULL");
     *out = nullptr;
     if (n_boxes < 1 || n_boxes > (1 << 20))
@@ -259,7 +304,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         return fail(nullptr, NF_EINVAL, "nf_init: radius must be 1, 2 or 3");
     if (softening != NF_SOFT_PLUMMER && softening != NF_SOFT_SPLINE)
         return fail(nullptr, NF_EINVAL, "nf_init: unsupported softening");
-    if (precision < NF_PREC_FP32 || precision > NF_PREC_FP64_REF)
+    if (precision < NF_PREC_FP32 || precision > NF_PREC_FP32_COMP_PAIR)
         return fail(nullptr, NF_EINVAL, "nf_init: unknown precision");
     if (softening == NF_SOFT_SPLINE && precision != NF_PREC_FP32)
         return fail(nullptr, NF_EINVAL, "nf_init: the spline softening is implemented for NF_PREC_FP32");
@@ -277,6 +322,12 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     }
     if (n_cells >= ((int64_t)1 << 30))
         return fail(nullptr, NF_EINVAL, "nf_init: total cells must stay below 2^30");
+    int64_t n_sink_cells = n_cells;
+    if (slab_nx > 0) {
+        // owned slabs and R ghost slabs on each side; owned cells come first
+        n_sink_cells = (int64_t)slab_nx * cpd[0] * cpd[0];
+        n_cells = (int64_t)(slab_nx + 2 * radius) * cpd[0] * cpd[0];
+    }
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -293,6 +344,8 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     c->softening = softening;
     c->capacity = capacity;
     c->n_cells = n_cells;
+    c->n_sink_cells = n_sink_cells;
+    c->slab = slab_nx > 0 ? 1 : 0;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     c->pow2_all = 1;
     int64_t off = 0;
@@ -311,6 +364,8 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         B.inv_h3 = (float)B.inv_h3_d;
         B.Lf = (float)L;
         B.inv_Lf = (float)(1.0 / L);
+        B.slab_x0 = slab_x0;
+        B.slab_nx = slab_nx;
         if (softening == NF_SOFT_SPLINE) {
             // pair factor inside eps_s: (10 - 15 u + 6 u^2) / eps_s^3, u = r / eps_s,
             // as c0 + c1 r + c2 r^2 in cell units; s gets a 1e-30 floor instead of eps^2
@@ -327,7 +382,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
         off += (int64_t)cpd[b] * cpd[b] * cpd[b];
     }
     const int64_t cap = capacity > 0 ? capacity : 1;
-    const int64_t tiles = nf::radix_tiles(cap);
+    const int64_t tiles = nf::sort_tiles(cap);
     c->max_tiles = tiles;
     cudaError_t e = cudaSuccess;
 #define NF_AL(p, cnt) if (!e) e = dalloc(&(p), (cnt))
@@ -339,9 +394,9 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     NF_AL(c->vals_b, cap);
     NF_AL(c->count, n_cells);
     NF_AL(c->cell_start, n_cells + 1);
-    const int64_t tmp_ints = std::max(nf::scan_tmp_ints(n_cells), nf::scan_tmp_ints(tiles * 256));
-    NF_AL(c->scan_tmp, tmp_ints);
-    NF_AL(c->radix_hist, tiles * 256 + 1);
+    NF_AL(c->scan_tmp, nf::scan_tmp_ints(n_cells));
+    NF_AL(c->sort_status, tiles * 256);
+    NF_AL(c->bin_state, 1);
     NF_AL(c->sorted, cap);
     if (precision == NF_PREC_FP64_REF) NF_AL(c->sorted_d, cap);
     NF_AL(c->w_sorted, cap);
@@ -356,6 +411,7 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->state_h), sizeof(nf::DevState));
     if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->mom_h), 4 * sizeof(double));
     if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->step_bits_h), sizeof(unsigned));
+    if (!e) e = cudaMallocHost(reinterpret_cast<void **>(&c->pin_i32), 4 * sizeof(int32_t));
     if (!e) e = cudaMemcpy(c->boxes_d, c->boxes_h.data(), sizeof(nf::BoxDev) * n_boxes, cudaMemcpyHostToDevice);
     if (!e) e = cudaMemset(c->state, 0, sizeof(nf::DevState));
     if (!e) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
@@ -373,11 +429,35 @@ int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const
     memset(c->state_h, 0, sizeof(nf::DevState));
     // default launch shape: 4 sinks per lane, 4 warps per block (FP32);
     // the compensated variant keeps 2 sinks per lane to stay clear of spills
-    c->tune = nf_tuning{4, 4, 0, 1, 2};
-    if (precision == NF_PREC_FP32_COMP) c->tune.sinks_per_lane = 2;
+    c->tune = nf_tuning{4, 4, 0, 1, 2, 0};
+    if (precision == NF_PREC_FP32_COMP || precision == NF_PREC_FP32_COMP_PAIR) c->tune.sinks_per_lane = 2;
     if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1, c->tune.vjp_sinks_per_lane = 1;
     *out = reinterpret_cast<nf_ctx *>(c);
     return NF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nf_init(nf_ctx **out, int device, int n_boxes, const double *box_size, const int *cpd,
+            int radius, const double *eps, int softening, int precision, int64_t capacity) {
+    return init_impl(out, device, n_boxes, box_size, cpd, radius, eps, softening, precision, capacity, 0, 0);
+}
+
+int nf_init_slab(nf_ctx **out, int device, double box_size, int cpd, int radius, double eps,
+                 int softening, int precision, int64_t capacity, int x_begin, int x_count) {
+    if (out) *out = nullptr;
+    if (radius < 1 || radius > nf::kMaxRadius)
+        return fail(nullptr, NF_EINVAL, "nf_init_slab: radius must be 1, 2 or 3");
+    if (cpd < 2 * radius + 1 || cpd > 1024)
+        return fail(nullptr, NF_EINVAL, "nf_init_slab: cpd must satisfy 2R+1 <= cpd <= 1024");
+    if (x_begin < 0 || x_begin >= cpd || x_count < radius || x_count > cpd)
+        return fail(nullptr, NF_EINVAL, "nf_init_slab: need 0 <= x_begin < cpd and R <= x_count <= cpd");
+    if (precision == NF_PREC_FP64_REF)
+        return fail(nullptr, NF_EINVAL, "nf_init_slab: FP32 precisions only (ghost records are FP32)");
+    return init_impl(out, device, 1, &box_size, &cpd, radius, &eps, softening, precision, capacity,
+                     x_begin, x_count);
 }
 
 void nf_free(nf_ctx *ctx) { release(reinterpret_cast<Ctx *>(ctx)); }
@@ -444,11 +524,15 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
     NF_CK(c, cudaStreamSynchronize(s));
     c->n = n;
     c->last_stream = s;
+    if (c->state_h->error & 2)
+        return fail(c, NF_ETIMEOUT, "nf_bin_particles: the cell sort's look-back gave up waiting");
     if (c->state_h->error) {
         return fail(c, NF_ERANGE, "nf_bin_particles: a position component is not finite or outside [0, L)");
     }
     c->binned = 1;
     c->have_momentum = 0;
+    c->ghosts_ready = 0;
+    c->n_ghost = 0;
     return NF_OK;
 }
 
@@ -516,6 +600,7 @@ int nf_compute_accel_vjp(nf_ctx *ctx, const float *w, float *grad_pos, void *str
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_compute_accel_vjp: no binned particles");
+    if (c->slab) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: not available on slab contexts");
     if (c->n > 0 && (!w || !grad_pos)) return fail(c, NF_EINVAL, "nf_compute_accel_vjp: w and grad_pos are required");
     const int K = vjp_k(c);
     int rc = ensure_decomp(c, K, s);
@@ -540,6 +625,7 @@ int nf_far_init(nf_ctx *ctx, int order, void *stream) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c) return fail(nullptr, NF_EINVAL, "nf_far_init: ctx is NULL");
     if (order < 1 || order > 8) return fail(c, NF_EINVAL, "nf_far_init: order must be in [1, 8]");
+    if (c->slab) return fail(c, NF_EINVAL, "nf_far_init: not available on slab contexts");
     for (const nf::BoxDev &B : c->boxes_h)
         if (B.cpd > 192) return fail(c, NF_EINVAL, "nf_far_init: CPD above 192 is not supported");
     DeviceGuard guard(c->device);
@@ -619,6 +705,9 @@ int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const float *ma
     if (!c) return fail(nullptr, NF_EINVAL, "nf_kdk_step: ctx is NULL");
     DeviceGuard guard(c->device);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_kdk_step: bin the positions and compute acc first");
+    if (c->slab)
+        return fail(c, NF_EINVAL, "nf_kdk_step: slab contexts exchange ghosts between binning and force; "
+                                  "use nf_kick, nf_drift, nf_bin_particles, nf_slab_import, nf_compute_accel");
     const int64_t n = c->n;
     int rc;
     if ((rc = nf_kick(ctx, vel, acc, 0.5 * dt, stream))) return rc;
@@ -636,6 +725,7 @@ int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, do
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (n < 0 || n > c->capacity) return fail(c, NF_EINVAL, "nf_accel_host: n must be in [0, capacity]");
+    if (c->slab) return fail(c, NF_EINVAL, "nf_accel_host: not available on slab contexts");
     if (n > 0 && (!pos_host || !acc_host)) return fail(c, NF_EINVAL, "nf_accel_host: pos_host and acc_host are required");
     if (n > c->st_cap || (mass_host && !c->st_mass)) {
         NF_CK(c, cudaStreamSynchronize(s));
@@ -650,7 +740,7 @@ int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, do
         c->st_cap = m;
     }
     if (n > 0) {
-        NF_CK(c, cudaMemcpyAsync(c->st_pos, pos_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        NF_CK(c, split_copy(c, c->st_pos, pos_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
         if (mass_host)
             NF_CK(c, cudaMemcpyAsync(c->st_mass, mass_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     }
@@ -660,7 +750,7 @@ int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, do
     rc = nf_compute_accel(ctx, c->st_acc, stream);
     if (rc) return rc;
     if (n > 0)
-        NF_CK(c, cudaMemcpyAsync(acc_host, c->st_acc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
+        NF_CK(c, split_copy(c, acc_host, c->st_acc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     NF_CK(c, cudaStreamSynchronize(s));
     return NF_OK;
 }
@@ -712,7 +802,7 @@ int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
 int nf_set_tuning(nf_ctx *ctx, const nf_tuning *t) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !t) return fail(c, NF_EINVAL, "nf_set_tuning: ctx and t are required");
-    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32], vjp_sinks_per_lane in {0,1,2,4}");
+    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32], vjp_sinks_per_lane in {0,1,2,4}, source_tile in {0,64,128,256}");
     if (c->precision == NF_PREC_FP64_REF && (t->sinks_per_lane != 1 || t->vjp_sinks_per_lane > 1))
         return fail(c, NF_EINVAL, "nf_set_tuning: FP64 reference contexts use one sink per lane");
     c->tune = *t;
@@ -732,13 +822,20 @@ int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
     DeviceGuard guard(c->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (!c->binned) return fail(c, NF_ESTATE, "nf_autotune: no binned particles");
+    if (c->slab && !c->ghosts_ready) return fail(c, NF_ESTATE, "nf_autotune: slab context without ghosts");
     if (reps < 1) reps = 1;
     std::vector<nf_tuning> cands;
     const int ks[] = {1, 2, 4};
     const int ws[] = {4, 8};
+    const bool tiles = c->precision != NF_PREC_FP64_REF && c->softening == NF_SOFT_PLUMMER;
+    const int ts[] = {64, 128, 256};
     for (int k : ks) {
         if (c->precision == NF_PREC_FP64_REF && k != 1) continue;
-        for (int w : ws) cands.push_back(nf_tuning{k, w, 0, c->tune.use_graph, c->tune.vjp_sinks_per_lane});
+        for (int w : ws)
+            for (int st : ts) {
+                if (!tiles && st != 128) continue;
+                cands.push_back(nf_tuning{k, w, 0, c->tune.use_graph, c->tune.vjp_sinks_per_lane, st});
+            }
     }
     float *acc = nullptr;
     NF_CK(c, dalloc(&acc, 3 * (c->n > 0 ? c->n : 1)));
@@ -778,6 +875,107 @@ int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
     if (!rc && best) *best = best_t;
     c->last_stream = s;
     return rc;
+}
+
+int nf_slab_export(nf_ctx *ctx, int side, int32_t *counts, float *records, int64_t records_cap,
+                   int64_t *n_records, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_slab_export: ctx is NULL");
+    if (!c->slab) return fail(c, NF_EINVAL, "nf_slab_export: not a slab context");
+    if (side != 0 && side != 1) return fail(c, NF_EINVAL, "nf_slab_export: side must be 0 or 1");
+    if (!n_records) return fail(c, NF_EINVAL, "nf_slab_export: n_records is required");
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_slab_export: no binned particles");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const nf::BoxDev &B = c->boxes_h[0];
+    const int64_t plane = (int64_t)B.cpd * B.cpd, ncell = (int64_t)c->R * plane;
+    // owned cells [c0, c0 + ncell): the first R owned slabs (side 0) or the last R (side 1)
+    const int64_t c0 = side == 0 ? 0 : (int64_t)(B.slab_nx - c->R) * plane;
+    int32_t *h = c->pin_i32;                   // pinned scratch for the two bounds
+    NF_CK(c, cudaMemcpyAsync(h, c->cell_start + c0, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaMemcpyAsync(h + 1, c->cell_start + c0 + ncell, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaStreamSynchronize(s));
+    const int64_t first = h[0], n = (int64_t)h[1] - h[0];
+    *n_records = n;
+    if (counts)
+        NF_CK(c, cudaMemcpyAsync(counts, c->count + c0, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, s));
+    if (records && n > 0) {
+        if (n > records_cap) return fail(c, NF_EINVAL, "nf_slab_export: records_cap is below n_records");
+        NF_CK(c, cudaMemcpyAsync(records, c->sorted + first, sizeof(float4) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_slab_import(nf_ctx *ctx, const int32_t *left_counts, const float *left_records, int64_t n_left,
+                   const int32_t *right_counts, const float *right_records, int64_t n_right, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_slab_import: ctx is NULL");
+    if (!c->slab) return fail(c, NF_EINVAL, "nf_slab_import: not a slab context");
+    if (!c->binned) return fail(c, NF_ESTATE, "nf_slab_import: bin the owned particles first");
+    if (!left_counts || !right_counts || n_left < 0 || n_right < 0 ||
+        (n_left > 0 && !left_records) || (n_right > 0 && !right_records))
+        return fail(c, NF_EINVAL, "nf_slab_import: both sides' counts, and their records when non-empty, are required");
+    if (c->n + n_left + n_right > c->capacity)
+        return fail(c, NF_EINVAL, "nf_slab_import: owned plus ghost particles exceed the capacity");
+    DeviceGuard guard(c->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    c->ghosts_ready = 0;
+    const nf::BoxDev &B = c->boxes_h[0];
+    const int64_t plane = (int64_t)B.cpd * B.cpd, ncell = (int64_t)c->R * plane;
+    const int64_t g0 = c->n_sink_cells;        // left ghost cells, then the right ones
+    NF_CK(c, cudaMemcpyAsync(c->count + g0, left_counts, sizeof(int) * ncell, cudaMemcpyDeviceToDevice, s));
+    NF_CK(c, cudaMemcpyAsync(c->count + g0 + ncell, right_counts, sizeof(int) * ncell,
+                             cudaMemcpyDeviceToDevice, s));
+    if (n_left > 0)
+        NF_CK(c, cudaMemcpyAsync(c->sorted + c->n, left_records, sizeof(float4) * n_left,
+                                 cudaMemcpyDeviceToDevice, s));
+    if (n_right > 0)
+        NF_CK(c, cudaMemcpyAsync(c->sorted + c->n + n_left, right_records, sizeof(float4) * n_right,
+                                 cudaMemcpyDeviceToDevice, s));
+    NF_CK(c, cudaMemsetAsync(&c->state->error, 0, sizeof(int), s));
+    NF_CK(c, nf::launch_check_counts(c->count + g0, 2 * ncell, &c->state->error, s));
+    NF_CK(c, nf::scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches));
+    // the ghost counts must be non-negative and add up to the records given
+    int32_t *h = c->pin_i32;
+    NF_CK(c, cudaMemcpyAsync(h, c->cell_start + g0 + ncell, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaMemcpyAsync(h + 1, c->cell_start + c->n_cells, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaMemcpyAsync(&c->state_h->error, &c->state->error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NF_CK(c, cudaStreamSynchronize(s));
+    if (c->state_h->error & 4)
+        return fail(c, NF_EINVAL, "nf_slab_import: a ghost count is negative");
+    if ((int64_t)h[0] != c->n + n_left || (int64_t)h[1] != c->n + n_left + n_right)
+        return fail(c, NF_EINVAL, "nf_slab_import: the ghost counts do not add up to n_left and n_right");
+    c->n_ghost = n_left + n_right;
+    c->ghosts_ready = 1;
+    c->last_stream = s;
+    return NF_OK;
+}
+
+int nf_slab_of(const float *pos, int64_t n, double box_size, int cpd, int32_t *slab, void *stream) {
+    if (n < 0 || (n > 0 && (!pos || !slab)))
+        return fail(nullptr, NF_EINVAL, "nf_slab_of: pos and slab are required for n > 0");
+    if (!(box_size > 0.0) || !std::isfinite(box_size) || cpd < 1 || cpd > 1024)
+        return fail(nullptr, NF_EINVAL, "nf_slab_of: box_size must be finite and > 0, 1 <= cpd <= 1024");
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, NF_ECUDA, "nf_slab_of: no usable current CUDA device");
+    }
+    nf::BoxDev B{};
+    B.L = box_size;
+    B.cpd_d = (double)cpd;
+    B.cpd = cpd;
+    B.Lf = (float)box_size;
+    B.inv_Lf = (float)(1.0 / box_size);
+    cudaError_t e = nf::launch_slab_of(pos, n, B, is_pow2(box_size) ? 1 : 0, sms, slab,
+                                       reinterpret_cast<cudaStream_t>(stream));
+    if (e) {
+        cudaGetLastError();
+        return fail(nullptr, NF_ECUDA, std::string("nf_slab_of: ") + cudaGetErrorString(e));
+    }
+    return NF_OK;
 }
 
 }  // extern "C"

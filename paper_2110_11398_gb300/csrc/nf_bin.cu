@@ -1,11 +1,23 @@
 // nf_bin.cu -- cell binning (the cubic cell lattice of Maksimova et al. 2021,
-// Sec. 3.1): per-particle cell id, per-cell count, exclusive prefix scan,
-// stable sort by cell (LSD radix sort whose digit ranks keep input order) and
-// the gather into cell-sorted float4 records of cell-relative coordinates.
+// Sec. 3.1): per-particle cell id, stable sort by cell and the cell-sorted
+// float4 records of cell-relative coordinates, then per-cell counts and the
+// exclusive prefix scan cell_start.
 //
 // Cell arithmetic, identical on every device and host: u = (x * CPD) / L in
 // IEEE double with no contraction, cell = floor(u) (CPD rounds down to
 // CPD-1), relative coordinate float32(u - (cell + 0.5)) in cell units.
+//
+// The sort is a least-significant-digit radix sort on the cell id with
+// 8-bit digits, one kernel per digit ("one sweep"): a tile of 4096 keys ranks
+// its keys by digit in input order (match_any within a warp, warps in
+// order), learns where each digit's run starts in the output from the tiles
+// before it by a decoupled look-back over per-tile digit counts, and writes
+// its keys digit-run by digit-run through shared memory, so the stores are
+// coalesced. The digit histograms of every pass are counted once, in the
+// kernel that computes the cell ids. The last pass writes the cell-sorted
+// records (reading each particle's position at its input index) instead of
+// the sort values, so no separate gather pass is needed. Per-cell counts come
+// from the run boundaries of the sorted keys.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,11 +34,13 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;                       // per thread
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kRadixThreads = 256;                  // 8 warps
-constexpr int kRadixItems = 16;                     // chunks of 32 per warp
-constexpr int kRadixWarps = kRadixThreads / 32;
-constexpr int kRadixTile = kRadixThreads * kRadixItems;  // 4096 keys
-constexpr int kRadixDigits = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kDigits = 256;
+static_assert(kSortThreads == kDigits, "one thread per digit in the per-digit steps");
+// Look-back spin limit: a tile waits for a predecessor's count at most this
+// many polls (with a short sleep between polls), then flags an error and
+// goes on; the host turns the flag into NF_ETIMEOUT.
+constexpr unsigned kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ int box_of_particle(const int64_t *poff, int n_boxes, int64_t i) {
     int lo = 0, hi = n_boxes - 1;
@@ -73,48 +87,73 @@ __device__ __forceinline__ bool cell_rel_pow2(float x, float cpd_f, float inv_L,
     return true;
 }
 
-// a1 + a2: cell id of every particle and per-cell counts.
-__global__ void k_cell_ids(const float *__restrict__ pos, int64_t n,
-                           const int64_t *__restrict__ poff, int n_boxes,
-                           const BoxDev *__restrict__ boxes, int pow2,
-                           int *__restrict__ cid, int *__restrict__ count,
-                           DevState *st) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const bool live = i < n;
-        int cell = -1;
-        if (live) {
-            const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
-            const BoxDev B = boxes[b];
-            int c3[3];
-            bool ok = true;
+// a1: the global cell id of a particle with coordinates x[3] in box B; ok is
+// false for a component outside [0, L) or not finite (false for NaN), and
+// such a particle goes to the box's first cell.
+__device__ __forceinline__ int particle_cell(const float x[3], const BoxDev &B, int pow2, bool &ok) {
+    int c3[3];
+    ok = true;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float xf = pos[3 * i + a];
-                // range test (false for NaN); for a power-of-two L, L is a
-                // float and the test is exact in FP32
-                const bool in = pow2 ? (xf >= 0.f && xf < B.Lf)
-                                     : ((double)xf >= 0.0 && (double)xf < B.L);
-                ok = ok && in;
-                int cc = 0;
-                float rr;
-                if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, cc, rr)))
-                    cc = cell_index(cell_unit((double)xf, B, pow2 != 0), B.cpd);
-                c3[a] = cc;
-            }
-            if (!ok) atomicOr(&st->error, 1);
-            cell = B.cell_off + (c3[0] * B.cpd + c3[1]) * B.cpd + c3[2];
-            cid[i] = cell;
+    for (int a = 0; a < 3; ++a) {
+        const float xf = x[a];
+        // for a power-of-two L, L is a float and the test is exact in FP32
+        const bool in = pow2 ? (xf >= 0.f && xf < B.Lf) : ((double)xf >= 0.0 && (double)xf < B.L);
+        ok = ok && in;
+        int cc = 0;
+        float rr;
+        if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, cc, rr)))
+            cc = cell_index(cell_unit((double)xf, B, pow2 != 0), B.cpd);
+        c3[a] = cc;
+    }
+    if (B.slab_nx > 0) {           // slab context: local x slab; other slabs are not owned
+        int lx = c3[0] - B.slab_x0;
+        if (lx < 0) lx += B.cpd;
+        if (lx >= B.slab_nx) {
+            ok = false;
+            lx = 0;
         }
-        // warp-aggregated histogram: particles in input order are often
-        // spatially coherent, so many lanes hit the same counter
-        const unsigned live_mask = __ballot_sync(0xffffffffu, live);
-        if (live) {
-            const unsigned peers = __match_any_sync(live_mask, cell);
-            if (lane == __ffs(peers) - 1) atomicAdd(&count[cell], __popc(peers));
+        c3[0] = lx;
+    }
+    return B.cell_off + (c3[0] * B.cpd + c3[1]) * B.cpd + c3[2];
+}
+
+// a5: cell-relative coordinates of a particle (cell units) as float, and as
+// double for the FP64 reference records.
+__device__ __forceinline__ void particle_rel(const float x[3], const BoxDev &B, int pow2, bool want_d,
+                                             float rf[3], double rd[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xf = x[a];
+        const double xd = (double)xf;
+        const bool in = pow2 ? (xf >= 0.f && xf < B.Lf) : (xd >= 0.0 && xd < B.L);
+        int c;
+        float r32;
+        if (in && !want_d && pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, c, r32)) {
+            rf[a] = r32;
+            rd[a] = (double)r32;
+        } else {
+            const double u = in ? cell_unit(xd, B, pow2 != 0) : 0.5;
+            c = in ? cell_index(u, B.cpd) : 0;
+            rd[a] = __dsub_rn(u, (double)c + 0.5);
+            rf[a] = __double2float_rn(rd[a]);
         }
     }
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
 // ------------------------------------------------------------ scan
@@ -204,128 +243,287 @@ __global__ void k_scan_apply(const int *__restrict__ in, int64_t n,
     }
 }
 
-// ------------------------------------------------------------ radix sort
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
+// ------------------------------------------------------------ cell ids + digit counts
+constexpr int kKeyThreads = 256;
+constexpr int kKeyPer = 4;                              // particles per thread per chunk
+constexpr int kKeyChunk = kKeyThreads * kKeyPer;        // 1024 particles, 12 KB of positions
 
-// Digit histogram of one tile; hist is digit-major: hist[d * ntiles + tile].
-__global__ void __launch_bounds__(kRadixThreads)
-k_radix_upsweep(const int *__restrict__ keys, int64_t n, int shift, int64_t ntiles,
-                int *__restrict__ hist) {
-    __shared__ int h[kRadixDigits];
-    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x) h[d] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * (32 * kRadixItems);
-#pragma unroll 4
-    for (int c = 0; c < kRadixItems; ++c) {
-        const int64_t idx = base + c * 32 + lane;
-        const bool live = idx < n;
-        const int d = live ? ((keys[idx] >> shift) & 0xff) : (0x100 + lane);
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (live && lane == __ffs(peers) - 1) atomicAdd(&h[d], __popc(peers));
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x)
-        hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
-}
-
-// Stable scatter of one tile: warps own consecutive sub-tiles, chunks of 32
-// are ranked in order with match_any, so equal digits keep input order.
-// vals_in == nullptr means the identity (first pass).
-__global__ void __launch_bounds__(kRadixThreads)
-k_radix_downsweep(const int *__restrict__ keys_in, const int *__restrict__ vals_in, int64_t n,
-                  int shift, int64_t ntiles, const int *__restrict__ hist_scanned,
-                  int *__restrict__ keys_out, int *__restrict__ vals_out, int write_keys) {
-    __shared__ int woff[kRadixWarps][kRadixDigits];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < kRadixWarps * kRadixDigits; d += blockDim.x)
-        (&woff[0][0])[d] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + warp * (32 * kRadixItems);
-    int key[kRadixItems], dig[kRadixItems];
-#pragma unroll
-    for (int c = 0; c < kRadixItems; ++c) {
-        const int64_t idx = base + c * 32 + lane;
-        const bool live = idx < n;
-        key[c] = live ? keys_in[idx] : 0;
-        dig[c] = live ? ((key[c] >> shift) & 0xff) : (0x100 + lane);
-    }
-    // per-warp digit counts
-#pragma unroll
-    for (int c = 0; c < kRadixItems; ++c) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
-        if (dig[c] < 0x100 && lane == __ffs(peers) - 1) woff[warp][dig[c]] += __popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    // exclusive scan over warps per digit, plus the tile's global base
-    for (int d = threadIdx.x; d < kRadixDigits; d += blockDim.x) {
-        int run = hist_scanned[(int64_t)d * ntiles + blockIdx.x];
-        for (int w = 0; w < kRadixWarps; ++w) {
-            int t = woff[w][d];
-            woff[w][d] = run;
-            run += t;
+// a1 for every particle (cell id into cid, range check), and the 8-bit digit
+// histograms of all `passes` radix passes (block-private in shared memory,
+// then added to the global counts). A block copies a chunk of 1024
+// positions into shared memory with coalesced 16-byte loads, then each
+// thread takes four particles from there.
+__global__ void __launch_bounds__(kKeyThreads) k_cell_keys(const float *__restrict__ pos, int64_t n,
+                                                           const int64_t *__restrict__ poff, int n_boxes,
+                                                           const BoxDev *__restrict__ boxes, int pow2,
+                                                           int passes, int *__restrict__ cid, BinState *bs,
+                                                           DevState *st) {
+    __shared__ __align__(16) float sp[3 * kKeyChunk];
+    __shared__ int h[kMaxSortPasses][kDigits];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int t = tid; t < kMaxSortPasses * kDigits; t += kKeyThreads) (&h[0][0])[t] = 0;
+    bool bad = false;
+    for (int64_t c0 = (int64_t)blockIdx.x * kKeyChunk; c0 < n; c0 += (int64_t)gridDim.x * kKeyChunk) {
+        const int cnt = (int)min((int64_t)kKeyChunk, n - c0);
+        const float *src = pos + 3 * c0;
+        __syncthreads();                       // previous chunk consumed
+        if (cnt == kKeyChunk && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+            const float4 *s4 = reinterpret_cast<const float4 *>(src);
+            float4 *d4 = reinterpret_cast<float4 *>(sp);
+            for (int t = tid; t < 3 * kKeyChunk / 4; t += kKeyThreads) d4[t] = s4[t];
+        } else {
+            for (int t = tid; t < 3 * cnt; t += kKeyThreads) sp[t] = src[t];
         }
-    }
-    __syncthreads();
-    const unsigned lt = lanemask_lt();
+        __syncthreads();
 #pragma unroll
-    for (int c = 0; c < kRadixItems; ++c) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[c]);
-        const bool live = dig[c] < 0x100;
-        int dest = 0;
-        if (live) dest = woff[warp][dig[c]] + __popc(peers & lt);
-        __syncwarp();
-        if (live && lane == __ffs(peers) - 1) woff[warp][dig[c]] += __popc(peers);
-        __syncwarp();
-        if (live) {
-            const int64_t idx = base + c * 32 + lane;
-            const int v = vals_in ? vals_in[idx] : (int)idx;
-            if (write_keys) keys_out[dest] = key[c];
-            vals_out[dest] = v;
-        }
-    }
-}
-
-// a4 + a5: sorted record k = particle perm[k]: cell-relative coordinates in
-// cell units and its mass.
-__global__ void k_gather(const float *__restrict__ pos, const float *__restrict__ mass, float m0,
-                         int64_t n, const int *__restrict__ perm,
-                         const int64_t *__restrict__ poff, int n_boxes,
-                         const BoxDev *__restrict__ boxes, int pow2,
-                         float4 *__restrict__ sorted, dbl4 *__restrict__ sorted_d) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int i = perm[k];
-        const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
-        const BoxDev B = boxes[b];
-        float rf[3];
-        double rd[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float xf = pos[3 * (int64_t)i + a];
-            const double x = (double)xf;
-            const bool in = pow2 ? (xf >= 0.f && xf < B.Lf) : (x >= 0.0 && x < B.L);
-            int c;
-            float r32;
-            if (in && !sorted_d && pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, c, r32)) {
-                rf[a] = r32;
-                rd[a] = (double)r32;
-            } else {
-                const double u = in ? cell_unit(x, B, pow2 != 0) : 0.5;
-                c = in ? cell_index(u, B.cpd) : 0;
-                rd[a] = __dsub_rn(u, (double)c + 0.5);
-                rf[a] = __double2float_rn(rd[a]);
+        for (int u = 0; u < kKeyPer; ++u) {
+            const int j = tid + u * kKeyThreads;
+            const bool live = j < cnt;
+            int cell = 0;
+            if (live) {
+                const int64_t i = c0 + j;
+                const int b = n_boxes == 1 ? 0 : box_of_particle(poff, n_boxes, i);
+                const float x[3] = {sp[3 * j], sp[3 * j + 1], sp[3 * j + 2]};
+                bool ok;
+                cell = particle_cell(x, boxes[b], pow2, ok);
+                bad = bad || !ok;
+                cid[i] = cell;
+            }
+            // a warp's particles often share the high digits (input order is
+            // often spatially coherent): then one add counts them all, else
+            // the lanes of each digit are counted by one add
+            const unsigned live_mask = __ballot_sync(0xffffffffu, live);
+            if (live_mask) {
+                for (int p = 0; p < passes; ++p) {
+                    const int d = (cell >> (8 * p)) & 0xff;
+                    if (live) {
+                        const unsigned peers = __match_any_sync(live_mask, d);
+                        if (lane == __ffs(peers) - 1) atomicAdd(&h[p][d], __popc(peers));
+                    }
+                }
             }
         }
-        const float m = mass ? mass[i] : B.gm;
-        sorted[k] = make_float4(rf[0], rf[1], rf[2], m);
-        if (sorted_d) sorted_d[k] = dbl4_make(rd[0], rd[1], rd[2], (double)m);
     }
+    if (bad) atomicOr(&st->error, 1);
+    __syncthreads();
+    for (int t = tid; t < passes * kDigits; t += kKeyThreads) {
+        const int v = (&h[0][0])[t];
+        if (v) atomicAdd(&bs->hist[t / kDigits][t % kDigits], v);
+    }
+}
+
+// ------------------------------------------------------------ one radix pass
+struct SortArgs {
+    const int *keys_in;
+    const int *vals_in;            // nullptr: values are the input indices (first pass)
+    int *keys_out;
+    int *vals_out;                 // last pass: the permutation (sorted slot -> input index)
+    int64_t n;
+    int shift;
+    int pass;
+    unsigned epoch;                // tags this pass's look-back words (unique per pass)
+    unsigned long long *status;    // [tiles][kDigits] look-back words
+    BinState *bs;
+    DevState *st;
+    // last pass: the cell-sorted records
+    const float *pos;
+    const float *mass;             // nullptr: per-box G m
+    const int64_t *poff;
+    int n_boxes;
+    const BoxDev *boxes;
+    int pow2;
+    float4 *sorted;
+    dbl4 *sorted_d;                // FP64 copy (FP64 reference contexts) or nullptr
+};
+
+// Look-back word of (tile, digit): high 32 bits 2 * epoch (the tile's own
+// count of that digit is published) or 2 * epoch + 1 (the inclusive count of
+// all tiles up to it is published), low 32 bits the count. Words of an
+// earlier pass carry another epoch and read as "not yet published".
+template <bool LAST>
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a) {
+    __shared__ int s_key[kSortTile];
+    __shared__ int s_val[kSortTile];
+    __shared__ int s_wcnt[kSortWarps][kDigits];
+    __shared__ int s_dstart[kDigits];
+    __shared__ int s_gbase[kDigits];
+    __shared__ int s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(&a.bs->tile_ctr[a.pass], 1);
+    for (int t = tid; t < kSortWarps * kDigits; t += kSortThreads) (&s_wcnt[0][0])[t] = 0;
+    // global start of each digit's output run: exclusive scan of the pass's
+    // digit histogram
+    int goff;
+    block_excl_scan(a.bs->hist[a.pass][tid], goff);
+    const int64_t tile = s_tile;
+    const int64_t t0 = tile * kSortTile;
+    const int64_t base = t0 + warp * (32 * kSortItems);
+    int key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        const int64_t idx = base + c * 32 + lane;
+        const bool live = idx < a.n;
+        key[c] = live ? a.keys_in[idx] : 0;
+        val[c] = live ? (a.vals_in ? a.vals_in[idx] : (int)idx) : 0;
+    }
+    // rank of each key among the warp's keys of the same digit, in input order
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        const bool live = base + c * 32 + lane < a.n;
+        const int d = live ? ((key[c] >> a.shift) & 0xff) : (0x100 + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        int r = 0;
+        if (live) r = s_wcnt[warp][d] + __popc(peers & lt);
+        __syncwarp();
+        if (live && lane == __ffs(peers) - 1) s_wcnt[warp][d] += __popc(peers);
+        __syncwarp();
+        rank[c] = r;
+    }
+    __syncthreads();
+    // thread tid = digit: warps' exclusive prefix of that digit and the tile's count
+    int cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+        const int t = s_wcnt[w][tid];
+        s_wcnt[w][tid] = cnt;
+        cnt += t;
+    }
+    int dstart;
+    block_excl_scan(cnt, dstart);
+    s_dstart[tid] = dstart;
+    // publish this tile's count of digit tid, then look back over the
+    // predecessors until one publishes an inclusive count
+    const unsigned hiA = 2u * a.epoch, hiP = 2u * a.epoch + 1u;
+    unsigned long long *mine = a.status + tile * kDigits + tid;
+    unsigned excl = 0;
+    if (tile == 0) {
+        st_relaxed(mine, ((unsigned long long)hiP << 32) | (unsigned)cnt);
+    } else {
+        st_relaxed(mine, ((unsigned long long)hiA << 32) | (unsigned)cnt);
+        int64_t p = tile - 1;
+        while (true) {
+            const unsigned long long *w = a.status + p * kDigits + tid;
+            unsigned long long v = ld_relaxed(w);
+            unsigned hi = (unsigned)(v >> 32);
+            unsigned spins = 0;
+            while (hi != hiA && hi != hiP) {
+                if (++spins >= kSpinLimit) break;
+                if (spins > 16) __nanosleep(100);
+                v = ld_relaxed(w);
+                hi = (unsigned)(v >> 32);
+            }
+            if (hi != hiA && hi != hiP) {       // gave up: flag it and go on
+                atomicOr(&a.st->error, 2);
+                break;
+            }
+            excl += (unsigned)v;
+            if (hi == hiP || p == 0) break;
+            --p;
+        }
+        st_relaxed(mine, ((unsigned long long)hiP << 32) | (excl + (unsigned)cnt));
+    }
+    s_gbase[tid] = goff + (int)excl - dstart;
+    __syncthreads();
+    // keys into shared memory in digit order (stable)
+#pragma unroll
+    for (int c = 0; c < kSortItems; ++c) {
+        if (base + c * 32 + lane < a.n) {
+            const int d = (key[c] >> a.shift) & 0xff;
+            const int slot = s_dstart[d] + s_wcnt[warp][d] + rank[c];
+            s_key[slot] = key[c];
+            s_val[slot] = val[c];
+        }
+    }
+    __syncthreads();
+    const int tile_n = (int)min((int64_t)kSortTile, a.n - t0);
+    if (!LAST) {
+        for (int j = tid; j < tile_n; j += kSortThreads) {
+            const int k = s_key[j];
+            const int dest = s_gbase[(k >> a.shift) & 0xff] + j;
+            a.keys_out[dest] = k;
+            a.vals_out[dest] = s_val[j];
+        }
+        return;
+    }
+    // last pass: the records. Positions are read at the input index, four
+    // slots per thread at a time so that the scattered loads overlap.
+    constexpr int U = 4;
+    for (int j0 = tid; j0 < tile_n; j0 += U * kSortThreads) {
+        float x[U][3];
+        int ii[U], kk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * kSortThreads;
+            ii[u] = 0;
+            kk[u] = 0;
+            if (j < tile_n) {
+                ii[u] = s_val[j];
+                kk[u] = s_key[j];
+                const float *p = a.pos + 3 * (int64_t)ii[u];
+                x[u][0] = p[0];
+                x[u][1] = p[1];
+                x[u][2] = p[2];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * kSortThreads;
+            if (j >= tile_n) continue;
+            const int i = ii[u];
+            const int b = a.n_boxes == 1 ? 0 : box_of_particle(a.poff, a.n_boxes, i);
+            const BoxDev &B = a.boxes[b];
+            float rf[3];
+            double rd[3];
+            particle_rel(x[u], B, a.pow2, a.sorted_d != nullptr, rf, rd);
+            const float m = a.mass ? a.mass[i] : B.gm;
+            const int dest = s_gbase[(kk[u] >> a.shift) & 0xff] + j;
+            a.sorted[dest] = make_float4(rf[0], rf[1], rf[2], m);
+            if (a.sorted_d) a.sorted_d[dest] = dbl4_make(rd[0], rd[1], rd[2], (double)m);
+            a.vals_out[dest] = i;
+            a.keys_out[dest] = kk[u];
+        }
+    }
+}
+
+// Per-cell counts from the runs of equal keys in the sorted key array: the
+// last element of a run adds its end, the first subtracts its start (each
+// cell gets one or two adds; count starts at zero).
+__global__ void k_cell_runs(const int *__restrict__ keys, int64_t n, int *__restrict__ count) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = keys[k];
+        const bool first = k == 0 || keys[k - 1] != c;
+        const bool last = k == n - 1 || keys[k + 1] != c;
+        if (first && last) count[c] = 1;
+        else if (first) atomicAdd(&count[c], -(int)k);
+        else if (last) atomicAdd(&count[c], (int)(k + 1));
+    }
+}
+
+// The global x slab of every particle (the x part of a1), or -1 for a
+// particle whose x is outside [0, L) or not finite.
+__global__ void k_slab_of(const float *__restrict__ pos, int64_t n, BoxDev B, int pow2,
+                          int32_t *__restrict__ slab) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float xf = pos[3 * i];
+        const bool in = pow2 ? (xf >= 0.f && xf < B.Lf) : ((double)xf >= 0.0 && (double)xf < B.L);
+        int c = -1;
+        float r;
+        if (in && !(pow2 && cell_rel_pow2(xf, (float)B.cpd, B.inv_Lf, B.cpd, c, r)))
+            c = cell_index(cell_unit((double)xf, B, pow2 != 0), B.cpd);
+        slab[i] = in ? c : -1;
+    }
+}
+
+// Sets bit 2 of *error_word if any of n counts is negative.
+__global__ void k_check_counts(const int *__restrict__ count, int64_t n, int *error_word) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad = bad || count[i] < 0;
+    if (bad) atomicOr(error_word, 4);
 }
 
 int grid_for(int64_t n, int threads, int sm_count, int per_sm = 8) {
@@ -371,54 +569,91 @@ int64_t scan_tmp_ints(int64_t n) {
     }
     return total;
 }
-int64_t radix_tiles(int64_t n) { return (n + kRadixTile - 1) / kRadixTile; }
+
+int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+cudaError_t launch_slab_of(const float *pos, int64_t n, const BoxDev &B, int pow2, int sm_count,
+                           int32_t *slab, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_slab_of<<<grid_for(n, 256, sm_count), 256, 0, s>>>(pos, n, B, pow2, slab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_counts(const int *count, int64_t n, int *error_word, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_check_counts<<<grid_for(n, 256, 152), 256, 0, s>>>(count, n, error_word);
+    return cudaGetLastError();
+}
+
+int sort_passes(int64_t n_cells) {
+    int bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < n_cells) ++bits;
+    const int p = (bits + 7) / 8;
+    return p < 1 ? 1 : p;
+}
 
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
                        cudaStream_t s) {
+    (void)m0;
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->count, 0, sizeof(int) * c->n_cells, s))) return e;
     if ((e = cudaMemsetAsync(&c->state->error, 0, sizeof(int), s))) return e;
-    if (n > 0) {
-        k_cell_ids<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(
-            pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, c->keys_a, c->count, c->state);
+    if (n == 0) {
+        c->perm = c->vals_a;
+        c->sorted_keys = c->keys_a;
+        return scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches);
+    }
+    const int passes = sort_passes(c->n_cells);
+    if ((e = cudaMemsetAsync(c->bin_state, 0, sizeof(BinState), s))) return e;
+    k_cell_keys<<<grid_for(n, kKeyChunk, c->sm_count), kKeyThreads, 0, s>>>(
+        pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, passes, c->keys_a, c->bin_state,
+        c->state);
+    if ((e = cudaGetLastError())) return e;
+    c->launches += 1;
+    // look-back words are told apart by an epoch per pass; when the counter
+    // would wrap, the words are cleared and the count restarts
+    if (c->bin_epoch + (unsigned)passes >= 0x7ffffff0u || c->bin_epoch == 0) {
+        if ((e = cudaMemsetAsync(c->sort_status, 0,
+                                 sizeof(unsigned long long) * kDigits * c->max_tiles, s)))
+            return e;
+        c->bin_epoch = 1;
+    }
+    const int64_t nt = sort_tiles(n);
+    SortArgs a{};
+    a.n = n;
+    a.status = c->sort_status;
+    a.bs = c->bin_state;
+    a.st = c->state;
+    a.pos = pos;
+    a.mass = mass;
+    a.poff = c->poff_d;
+    a.n_boxes = c->n_boxes;
+    a.boxes = c->boxes_d;
+    a.pow2 = c->pow2_all;
+    a.sorted = c->sorted;
+    a.sorted_d = c->precision == NF_PREC_FP64_REF ? c->sorted_d : nullptr;
+    for (int p = 0; p < passes; ++p) {
+        const bool even = (p & 1) == 0;
+        a.keys_in = even ? c->keys_a : c->keys_b;
+        a.vals_in = p == 0 ? nullptr : (even ? c->vals_a : c->vals_b);
+        a.keys_out = even ? c->keys_b : c->keys_a;
+        a.vals_out = even ? c->vals_b : c->vals_a;
+        a.shift = 8 * p;
+        a.pass = p;
+        a.epoch = c->bin_epoch++;
+        if (p == passes - 1)
+            k_sort_pass<true><<<(unsigned)nt, kSortThreads, 0, s>>>(a);
+        else
+            k_sort_pass<false><<<(unsigned)nt, kSortThreads, 0, s>>>(a);
         if ((e = cudaGetLastError())) return e;
         c->launches += 1;
     }
-    if ((e = scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches))) return e;
-    if (n == 0) {
-        c->perm = c->vals_a;
-        return cudaSuccess;
-    }
-    // passes of 8 bits over the used key bits
-    int bits = 0;
-    while (bits < 31 && ((int64_t)1 << bits) < c->n_cells) ++bits;
-    const int passes = bits <= 8 ? 1 : (bits + 7) / 8;
-    const int64_t nt = radix_tiles(n);
-    int *kin = c->keys_a, *kout = c->keys_b;
-    int *vin = nullptr, *vout = c->vals_a;
-    for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_radix_upsweep<<<(unsigned)nt, kRadixThreads, 0, s>>>(kin, n, shift, nt, c->radix_hist);
-        if ((e = cudaGetLastError())) return e;
-        if ((e = scan_exclusive(c->radix_hist, c->radix_hist, nt * kRadixDigits, c->scan_tmp, s,
-                                    &c->launches)))
-            return e;
-        const int last = p == passes - 1;
-        k_radix_downsweep<<<(unsigned)nt, kRadixThreads, 0, s>>>(
-            kin, vin, n, shift, nt, c->radix_hist, kout, vout, !last);
-        if ((e = cudaGetLastError())) return e;
-        c->launches += 2;
-        // ping-pong
-        int *t = kin; kin = kout; kout = t;
-        vin = vout;
-        vout = (vout == c->vals_a) ? c->vals_b : c->vals_a;
-    }
-    c->perm = vin;
-    k_gather<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(
-        pos, mass, m0, n, c->perm, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, c->sorted,
-        c->precision == NF_PREC_FP64_REF ? c->sorted_d : nullptr);
+    c->sorted_keys = a.keys_out;
+    c->perm = a.vals_out;
+    k_cell_runs<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(c->sorted_keys, n, c->count);
+    if ((e = cudaGetLastError())) return e;
     c->launches += 1;
-    return cudaGetLastError();
+    return scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches);
 }
 
 }  // namespace nf
@@ -439,7 +674,7 @@ namespace {
 
 constexpr int64_t kNoAllocMaxParticles = int64_t(1) << 20;   // 1,048,576
 constexpr int64_t kNoAllocMaxCells = int64_t(1) << 18;       // CPD^3 <= 262,144
-constexpr int64_t kNoAllocTiles = (kNoAllocMaxParticles + nf::kRadixTile - 1) / nf::kRadixTile;
+constexpr int64_t kNoAllocTiles = (kNoAllocMaxParticles + nf::kSortTile - 1) / nf::kSortTile;
 constexpr int64_t kNoAllocScanInts = 256;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -448,12 +683,14 @@ constexpr size_t kOffKeysB = kOffKeysA + align256(4 * kNoAllocMaxParticles);
 constexpr size_t kOffValsA = kOffKeysB + align256(4 * kNoAllocMaxParticles);
 constexpr size_t kOffValsB = kOffValsA + align256(4 * kNoAllocMaxParticles);
 constexpr size_t kOffCount = kOffValsB + align256(4 * kNoAllocMaxParticles);
-constexpr size_t kOffHist = kOffCount + align256(4 * kNoAllocMaxCells);
-constexpr size_t kOffScan = kOffHist + align256(4 * (nf::kRadixDigits * kNoAllocTiles + 1));
+constexpr size_t kOffStatus = kOffCount + align256(4 * kNoAllocMaxCells);
+constexpr size_t kOffBinState = kOffStatus + align256(8 * 256 * kNoAllocTiles);
+constexpr size_t kOffScan = kOffBinState + align256(sizeof(nf::BinState));
 constexpr size_t kOffState = kOffScan + align256(4 * kNoAllocScanInts);
 constexpr size_t kOffBox = kOffState + align256(sizeof(nf::DevState));
 constexpr size_t kOffPoff = kOffBox + align256(sizeof(nf::BoxDev));
 constexpr size_t kNoAllocBytes = kOffPoff + align256(2 * sizeof(int64_t));   // about 17.3 MB
+static_assert(kNoAllocScanInts >= (kNoAllocMaxCells + 4095) / 4096 + 1, "scan scratch");
 
 // Shared by every call on a device and kept (with the last call's contents)
 // until the process exits.
@@ -463,11 +700,12 @@ constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 unsigned char *g_noalloc_base[kNoAllocMaxDevices] = {};
 int g_noalloc_sms[kNoAllocMaxDevices] = {};
+unsigned g_noalloc_epoch[kNoAllocMaxDevices] = {};
 
 // Device address of the array on the current device. In host code the
 // array's name is only a host-side stand-in, so the address is looked up
 // once per device with that device current.
-int noalloc_setup(int dev, unsigned char **base, int *sms) {
+int noalloc_setup(int dev, unsigned char **base, int *sms, unsigned **epoch) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_base[dev]) {
         void *p = nullptr;
@@ -486,6 +724,7 @@ int noalloc_setup(int dev, unsigned char **base, int *sms) {
     }
     *base = g_noalloc_base[dev];
     *sms = g_noalloc_sms[dev];
+    *epoch = &g_noalloc_epoch[dev];
     return NF_OK;
 }
 
@@ -525,7 +764,8 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
     }
     unsigned char *base = nullptr;
     int sms = 0;
-    if (noalloc_setup(dev, &base, &sms) != NF_OK) {
+    unsigned *epoch = nullptr;
+    if (noalloc_setup(dev, &base, &sms, &epoch) != NF_OK) {
         set_thread_error("nf_bin_cells_noalloc: cudaGetSymbolAddress of the scratch array failed");
         return NF_ECUDA;
     }
@@ -545,7 +785,10 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
     c.vals_a = reinterpret_cast<int *>(base + kOffValsA);
     c.vals_b = reinterpret_cast<int *>(base + kOffValsB);
     c.count = reinterpret_cast<int *>(base + kOffCount);
-    c.radix_hist = reinterpret_cast<int *>(base + kOffHist);
+    c.sort_status = reinterpret_cast<unsigned long long *>(base + kOffStatus);
+    c.max_tiles = kNoAllocTiles;
+    c.bin_state = reinterpret_cast<BinState *>(base + kOffBinState);
+    c.bin_epoch = *epoch;
     c.scan_tmp = reinterpret_cast<int *>(base + kOffScan);
     c.state = reinterpret_cast<DevState *>(base + kOffState);
     c.boxes_d = reinterpret_cast<BoxDev *>(base + kOffBox);
@@ -571,6 +814,7 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
     cudaError_t e = cudaMemcpyAsync(c.boxes_d, &B, sizeof(B), cudaMemcpyHostToDevice, s);
     if (!e) e = cudaMemcpyAsync(c.poff_d, poff, sizeof(poff), cudaMemcpyHostToDevice, s);
     if (!e) e = launch_bin(&c, pos, mass, (float)mass_if_null, n, s);
+    *epoch = c.bin_epoch;
     if (!e && n > 0) e = cudaMemcpyAsync(perm, c.perm, sizeof(int) * n, cudaMemcpyDeviceToDevice, s);
     int err_word = 0;
     if (!e) e = cudaMemcpyAsync(&err_word, &c.state->error, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -579,6 +823,10 @@ extern "C" NF_API int nf_bin_cells_noalloc(const float *pos, const float *mass, 
         cudaGetLastError();
         set_thread_error(cudaGetErrorString(e));
         return NF_ECUDA;
+    }
+    if (err_word & 2) {
+        set_thread_error("nf_bin_cells_noalloc: the sort's look-back gave up waiting");
+        return NF_ETIMEOUT;
     }
     if (err_word) {
         set_thread_error("nf_bin_cells_noalloc: a position component is not finite or outside [0, L)");

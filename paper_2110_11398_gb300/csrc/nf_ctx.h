@@ -28,7 +28,11 @@ struct Ctx {
     int precision = NF_PREC_FP32;
     int softening = NF_SOFT_PLUMMER;
     int64_t capacity = 0;
-    int64_t n_cells = 0;          // total over boxes
+    int64_t n_cells = 0;          // total over boxes (a slab context: owned and ghost cells)
+    int64_t n_sink_cells = 0;     // cells whose particles are sinks (all but a slab context's ghosts)
+    int slab = 0;                 // 1: a slab context (one box, owned x slabs + R ghost slabs a side)
+    int ghosts_ready = 0;         // slab context: ghosts imported since the last binning
+    int64_t n_ghost = 0;          // slab context: ghost records behind the owned ones
     int sm_count = 0;
     int pow2_all = 0;             // every box side is a power of two
 
@@ -41,10 +45,13 @@ struct Ctx {
     int *keys_a = nullptr, *keys_b = nullptr;     // [capacity]
     int *vals_a = nullptr, *vals_b = nullptr;     // [capacity]
     int *perm = nullptr;                           // alias of the final values buffer
+    int *sorted_keys = nullptr;                    // alias of the final keys buffer (cell ids, sorted)
     int *count = nullptr;                          // [n_cells]
     int *cell_start = nullptr;                     // [n_cells + 1]
     int *scan_tmp = nullptr;                       // block sums of the scans
-    int *radix_hist = nullptr;                     // [256 * max_tiles + 1]
+    unsigned long long *sort_status = nullptr;     // [256 * max_tiles] look-back words of the sort
+    BinState *bin_state = nullptr;                 // digit histograms and tile counters
+    unsigned bin_epoch = 0;                        // tag of the next sort pass (0: words not yet cleared)
     int64_t max_tiles = 0;
     float4 *sorted = nullptr;                      // [capacity] (rx, ry, rz, m)
     dbl4 *sorted_d = nullptr;                   // [capacity] FP64 copy (FP64_REF only)
@@ -65,6 +72,7 @@ struct Ctx {
     double *mom_h = nullptr;                       // pinned [4]
     unsigned *step_bits = nullptr;                 // [1] timestep criterion (float bits)
     unsigned *step_bits_h = nullptr;               // pinned mirror
+    int32_t *pin_i32 = nullptr;                    // pinned [4]: small reads of cell_start
 
     // last binning
     int64_t n = 0;
@@ -82,6 +90,8 @@ struct Ctx {
     // host-buffer staging for nf_accel_host
     float *st_pos = nullptr, *st_mass = nullptr, *st_acc = nullptr;
     int64_t st_cap = 0;
+    cudaStream_t cp_streams[4] = {nullptr, nullptr, nullptr, nullptr};   // split host copies
+    cudaEvent_t cp_events[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
 
     // timing of the last binning / pair kernel, and the launch counter
     cudaEvent_t ev_bin0 = nullptr, ev_bin1 = nullptr, ev_pair0 = nullptr, ev_pair1 = nullptr;

@@ -19,6 +19,20 @@ constexpr int kBuckets = 64;
 // Max items one remainder of a cell can be cut into (see make_decomp()).
 constexpr int kDecompMax = 8;
 
+// Cell sort (nf_bin.cu): threads per tile, keys per thread, keys per tile,
+// and the most 8-bit digit passes a cell id can need (ids stay below 2^31).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxSortPasses = 4;
+
+// Device counters of one binning: the digit histogram of every radix pass
+// (counted with the cell ids) and each pass's dynamic tile counter.
+struct BinState {
+    int hist[kMaxSortPasses][256];
+    int tile_ctr[kMaxSortPasses];
+};
+
 // Four doubles, 32-byte aligned (cell-sorted FP64 record x, y, z, m).
 struct __align__(32) dbl4 {
     double x, y, z, w;
@@ -49,7 +63,22 @@ struct BoxDev {
     float Lf;          // L as float (exact when L is a power of two)
     float inv_Lf;      // 1 / L as float (exact when L is a power of two)
     double gm_d;       // same G m, double
+    int slab_x0;       // slab contexts: first owned x slab (global index)
+    int slab_nx;       // slab contexts: owned x slabs; 0 for a whole periodic box
 };
+
+// x index of the cell row at offset dx from local x slab cx. A whole box
+// wraps periodically. A slab context keeps its owned slabs at local x
+// 0..nx-1, then the R ghost slabs on its left (global x0-R..x0-1) at
+// nx..nx+R-1 and the R on its right (global x0+nx..x0+nx+R-1) at
+// nx+R..nx+2R-1, so an owned sink's neighbours never wrap.
+__host__ __device__ __forceinline__ int nbr_slab(const BoxDev &B, int cx, int dx, int R) {
+    const int t = cx + dx;
+    if (B.slab_nx == 0) return t < 0 ? t + B.cpd : (t >= B.cpd ? t - B.cpd : t);
+    if (t < 0) return B.slab_nx + R + t;
+    if (t >= B.slab_nx) return B.slab_nx + R + (t - B.slab_nx);
+    return t;
+}
 
 // One unit of pair work: `n` consecutive cell-sorted sinks of one cell,
 // processed by one warp whose lanes are split `1 << log2s` ways over sources.
@@ -62,7 +91,8 @@ struct __align__(16) WorkItem {
 
 // Device-resident counters of one context.
 struct DevState {
-    int error;                   // bit 0: a position outside [0, L) or not finite
+    int error;                   // bit 0: a position outside [0, L) or not finite;
+                                 // bit 1: the cell sort's look-back gave up waiting
     int n_items;                 // items written by the last work-list build
     int queue_head;              // persistent-kernel work counter
     int max_occ;                 // largest cell population
@@ -157,6 +187,9 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
                          float *dens = nullptr);
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);
 cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s);
+cudaError_t launch_slab_of(const float *pos, int64_t n, const BoxDev &B, int pow2, int sm_count,
+                           int32_t *slab, cudaStream_t s);
+cudaError_t launch_check_counts(const int *count, int64_t n, int *error_word, cudaStream_t s);
 void make_decomp(int k, Decomp *d);
 cudaError_t launch_kick(Ctx *c, float *vel, const float *acc, double h, cudaStream_t s);
 cudaError_t launch_drift(Ctx *c, float *pos, const float *vel, double dt, cudaStream_t s);
@@ -165,5 +198,6 @@ cudaError_t launch_cell_timestep(Ctx *c, const float *vel, const float *acc, uns
 cudaError_t scan_exclusive(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s,
                            int64_t *launches);
 int64_t scan_tmp_ints(int64_t n);
-int64_t radix_tiles(int64_t n);
+int64_t sort_tiles(int64_t n);
+int sort_passes(int64_t n_cells);
 }  // namespace nf

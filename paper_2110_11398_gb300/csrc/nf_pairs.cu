@@ -39,7 +39,7 @@ __device__ __forceinline__ int cell_nsrc(const BoxDev &B, int local, const int *
     const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
     int s = 0;
     for (int dx = -R; dx <= R; ++dx) {
-        const int x = wrapc(cx + dx, cpd);
+        const int x = nbr_slab(B, cx, dx, R);
         for (int dy = -R; dy <= R; ++dy) {
             const int row = B.cell_off + (x * cpd + wrapc(cy + dy, cpd)) * cpd;
             for (int dz = -R; dz <= R; ++dz) s += count[row + wrapc(cz + dz, cpd)];
@@ -62,7 +62,7 @@ struct WLArgs {
     int n_boxes;
     int R;
     int K;
-    int64_t n_cells;
+    int64_t n_cells;           // cells that hold sinks (a slab context's owned cells come first)
     const int *count;
     const int *cell_start;
     int *nsrc_cell;
@@ -229,7 +229,7 @@ __device__ __forceinline__ int build_table(const PairArgs &a, const BoxDev &B, i
         if (ci < a.nbr) {
             const int ix = ci / (W * W), iy = (ci / W) % W, iz = ci % W;
             const int g = B.cell_off +
-                          (wrapc(cx + ix - R, cpd) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
+                          (nbr_slab(B, cx, ix - R, R) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
                           wrapc(cz + iz - R, cpd);
             st = a.cell_start[g];
             cnt = a.cell_start[g + 1] - st;
@@ -274,7 +274,10 @@ __device__ __forceinline__ void two_sum1(float a, float b, float &s, float &e) {
 }
 
 // Forward pair kernel. K sinks per lane; EQ: all masses equal (applied in
-// the epilogue); COMP: per-sink sums kept as compensated (hi, lo) pairs.
+// the epilogue); COMP: 0 plain FP32 sums; 1 the per-tile FP32 partial sums
+// are folded into a compensated (hi, lo) running total by TwoSum (three per
+// sink and tile; the pair loop is the plain one); 2 every pair term is added
+// by TwoSum (the most accurate and the slowest form).
 // LAW 0: Plummer, f = s^-3/2 with s = r^2 + eps^2.
 // LAW 1: spline, f = min(c0 + c1 r + c2 r^2, r^-3): the polynomial is the
 //   law inside eps_s and r^-3 outside, and the two cross only at r = eps_s
@@ -283,14 +286,15 @@ __device__ __forceinline__ void two_sum1(float a, float b, float &s, float &e) {
 //   1e-30 floor so that the self pair gives a finite f times a zero offset.
 // KDE: also accumulate the density sum_j m_j max(0, 1 - r^2/b^2)
 //   (Sec. 3.3), with 1 - r^2/b^2 = kb0 + kb1 s.
-template <int K, bool EQ, bool COMP, int LAW = 0, bool KDE = false>
+// TILE: sources staged per tile (64, 128 or 256).
+template <int K, bool EQ, int COMP, int LAW = 0, bool KDE = false, int TILE = kTile>
 __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     constexpr int NF = EQ ? 3 : 4;
-    float *sbase = reinterpret_cast<float *>(smem_raw) + wib * (NF * kTile + 3 * a.tbl);
-    float *sx = sbase, *sy = sbase + kTile, *sz = sbase + 2 * kTile, *sm = sbase + 3 * kTile;
-    int *pfx = reinterpret_cast<int *>(sbase + NF * kTile);
+    float *sbase = reinterpret_cast<float *>(smem_raw) + wib * (NF * TILE + 3 * a.tbl);
+    float *sx = sbase, *sy = sbase + TILE, *sz = sbase + 2 * TILE, *sm = sbase + 3 * TILE;
+    int *pfx = reinterpret_cast<int *>(sbase + NF * TILE);
     int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
     const int n_items = a.st->n_items;
 
@@ -334,8 +338,8 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             rho[k] = 0ull;
         }
         int ci = 0, co = 0;   // cell stream: current neighbour cell, sources taken from it
-        for (int q0 = 0; q0 < nsrc; q0 += kTile) {
-            const int cntT = min(kTile, nsrc - q0);
+        for (int q0 = 0; q0 < nsrc; q0 += TILE) {
+            const int cntT = min(TILE, nsrc - q0);
             const int npair = (cntT + 1) >> 1;
             // fill the tile cell by cell: each cell's sources are contiguous in
             // the sorted array and share one offset d, so the lanes copy
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                         tr[k] = EQ ? f2_add(tr[k], t) : f2_fma(t, m2, tr[k]);
                     }
                     if (!EQ) f = f2_mul(f, m2);
-                    if (!COMP) {
+                    if (COMP != 2) {
                         tx[k] = f2_fma(f, dx, tx[k]);
                         ty[k] = f2_fma(f, dy, ty[k]);
                         tz[k] = f2_fma(f, dz, tz[k]);
@@ -419,12 +423,20 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     }
                 }
             }
-            if (!COMP) {
+            if (COMP == 0) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     ax[k] = f2_add(ax[k], tx[k]);
                     ay[k] = f2_add(ay[k], ty[k]);
                     az[k] = f2_add(az[k], tz[k]);
+                }
+            } else if (COMP == 1) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    f2_t e;
+                    two_sum(ax[k], tx[k], ax[k], e); lx[k] = f2_add(lx[k], e);
+                    two_sum(ay[k], ty[k], ay[k], e); ly[k] = f2_add(ly[k], e);
+                    two_sum(az[k], tz[k], az[k], e); lz[k] = f2_add(lz[k], e);
                 }
             }
             if (KDE) {
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
             for (int c = 0; c < 3; ++c) {
                 float h0, h1;
                 f2_unpack(hs[c], h0, h1);
-                if (!COMP) {
+                if (COMP == 0) {
                     float s = h0 + h1;
                     for (int o = 1; o < S; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
                     v[c] = s;
@@ -910,28 +922,32 @@ void *fptr(F f) { return reinterpret_cast<void *>(f); }
 void *pair_kernel_ext(int K, int eq, int law, int kde) {
 #define NF_SEL2(KK, EE)                                                          \
     if (K == KK && eq == EE) {                                                   \
-        if (law == 0) return fptr(k_pairs<KK, EE, false, 0, true>);              \
-        return kde ? fptr(k_pairs<KK, EE, false, 1, true>)                       \
-                   : fptr(k_pairs<KK, EE, false, 1, false>);                     \
+        if (law == 0) return fptr(k_pairs<KK, EE, 0, 0, true>);                  \
+        return kde ? fptr(k_pairs<KK, EE, 0, 1, true>)                           \
+                   : fptr(k_pairs<KK, EE, 0, 1, false>);                         \
     }
     NF_SEL2(1, 0) NF_SEL2(1, 1) NF_SEL2(2, 0) NF_SEL2(2, 1) NF_SEL2(4, 0) NF_SEL2(4, 1)
 #undef NF_SEL2
     return nullptr;
 }
 
-void *pair_kernel(int prec, int K, int eq, int law = 0, int kde = 0) {
+void *pair_kernel(int prec, int K, int eq, int law = 0, int kde = 0, int tile = kTile) {
     if (prec == NF_PREC_FP64_REF) return fptr(k_pairs_f64);
     if (law != 0 || kde) return prec == NF_PREC_FP32 ? pair_kernel_ext(K, eq, law, kde) : nullptr;
-    const bool comp = prec == NF_PREC_FP32_COMP;
-#define NF_SEL(KK)                                                                       \
-    if (K == KK) {                                                                       \
-        if (eq) return comp ? fptr(k_pairs<KK, true, true>) : fptr(k_pairs<KK, true, false>); \
-        return comp ? fptr(k_pairs<KK, false, true>) : fptr(k_pairs<KK, false, false>);  \
+    const int comp = prec == NF_PREC_FP32_COMP ? 1 : (prec == NF_PREC_FP32_COMP_PAIR ? 2 : 0);
+#define NF_SELT(KK, EE, CC)                                                               \
+    if (K == KK && eq == EE && comp == CC) {                                              \
+        if (tile == 64) return fptr(k_pairs<KK, EE, CC, 0, false, 64>);                   \
+        if (tile == 256) return fptr(k_pairs<KK, EE, CC, 0, false, 256>);                 \
+        return fptr(k_pairs<KK, EE, CC, 0, false, 128>);                                  \
     }
+#define NF_SEL(KK) \
+    NF_SELT(KK, 1, 0) NF_SELT(KK, 1, 1) NF_SELT(KK, 1, 2) NF_SELT(KK, 0, 0) NF_SELT(KK, 0, 1) NF_SELT(KK, 0, 2)
     NF_SEL(1)
     NF_SEL(2)
     NF_SEL(4)
 #undef NF_SEL
+#undef NF_SELT
     return nullptr;
 }
 
@@ -954,14 +970,14 @@ int table_stride(int R) {
     return (nbr + 1 + 3) & ~3;
 }
 
-size_t smem_per_warp(int prec, int R, int eq, int vjp) {
+size_t smem_per_warp(int prec, int R, int eq, int vjp, int tile = kTile) {
     const int tbl = table_stride(R);
     if (prec == NF_PREC_FP64_REF) {
         const int nf = vjp ? 7 : 4;
         return sizeof(double) * (size_t)(nf * kTile + (3 * tbl + 1) / 2);
     }
     const int nf = vjp ? (eq ? 6 : 7) : (eq ? 3 : 4);
-    return sizeof(float) * (size_t)(nf * kTile + 3 * tbl);
+    return sizeof(float) * (size_t)(nf * (vjp ? kTile : tile) + 3 * tbl);
 }
 
 cudaError_t prepare(void *fn, size_t smem) {
@@ -969,9 +985,9 @@ cudaError_t prepare(void *fn, size_t smem) {
 }
 
 cudaError_t launch_generic(Ctx *c, void *fn, int vjp, const PairArgs &args, const nf_tuning &t,
-                           cudaStream_t s) {
+                           cudaStream_t s, int tile = kTile) {
     const int warps = t.warps_per_block;
-    const size_t smem = smem_per_warp(c->precision, c->R, c->equal_mass, vjp) * warps;
+    const size_t smem = smem_per_warp(c->precision, c->R, c->equal_mass, vjp, tile) * warps;
     cudaError_t e = prepare(fn, smem);
     if (e) return e;
     int per_sm = t.blocks_per_sm;
@@ -1056,14 +1072,14 @@ cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
     a.n_boxes = c->n_boxes;
     a.R = c->R;
     a.K = c->decomp_k;
-    a.n_cells = c->n_cells;
+    a.n_cells = c->n_sink_cells;
     a.count = c->count;
     a.cell_start = c->cell_start;
     a.nsrc_cell = c->nsrc_cell;
     a.decomp = c->decomp_d + (c->decomp_k == 1 ? 0 : (c->decomp_k == 2 ? 1 : 2));
     a.st = c->state;
     a.items = c->items;
-    const unsigned blocks = (unsigned)((c->n_cells + 255) / 256);
+    const unsigned blocks = (unsigned)((c->n_sink_cells + 255) / 256 + (c->n_sink_cells == 0));
     k_wl_count<<<blocks, 256, 0, s>>>(a);
     k_wl_scan<<<1, 32, 0, s>>>(c->state);
     k_wl_write<<<blocks, 256, 0, s>>>(a);
@@ -1075,11 +1091,14 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
                          float *dens) {
     const int K = c->precision == NF_PREC_FP64_REF ? 1 : t.sinks_per_lane;
     const int law = c->softening == NF_SOFT_SPLINE ? 1 : 0;
-    void *fn = pair_kernel(c->precision, K, c->equal_mass, law, dens != nullptr);
+    // the source tile is a tuning choice of the plain Plummer kernels only
+    const int tile = (law == 0 && !dens && c->precision != NF_PREC_FP64_REF && t.source_tile) ? t.source_tile
+                                                                                             : kTile;
+    void *fn = pair_kernel(c->precision, K, c->equal_mass, law, dens != nullptr, tile);
     if (!fn) return cudaErrorInvalidValue;
     PairArgs args = make_args(c, acc, out_f64);
     args.dens = dens;
-    return launch_generic(c, fn, 0, args, t, s);
+    return launch_generic(c, fn, 0, args, t, s, tile);
 }
 
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s) {

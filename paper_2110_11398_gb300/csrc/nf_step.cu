@@ -124,9 +124,9 @@ cudaError_t launch_cell_timestep(Ctx *c, const float *vel, const float *acc, uns
                                  cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(best_bits, 0x7f, sizeof(unsigned), s);   // 0x7f7f7f7f: a huge float
     if (e) return e;
-    const int64_t threads = 32 * c->n_cells;
+    const int64_t threads = 32 * c->n_sink_cells;
     k_cell_timestep<<<grid_for(threads, 256, c->sm_count), 256, 0, s>>>(vel, acc, c->cell_start, c->perm,
-                                                                        c->n_cells, best_bits);
+                                                                        c->n_sink_cells, best_bits);
     c->launches += 1;
     return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ class NearField:
     Parameters follow the statement of the near-field problem (Maksimova et
     al. 2021, Sec. 3.1): box side ``box_size``, cells per dimension ``cpd``,
     near-field radius ``radius`` in cells and the Plummer softening ``eps``.
-    ``precision`` is "fp32", "fp32_comp" or "fp64". ``capacity`` is the
+    ``precision`` is "fp32", "fp32_comp" (tile sums folded with TwoSum),
+    "fp32_comp_pair" (every pair term added with TwoSum) or "fp64". ``capacity`` is the
     largest total particle count that will be binned.
     """
 
@@ -308,16 +309,17 @@ class NearField:
         N.check(self._lib.nf_get_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_get_tuning")
         return {"sinks_per_lane": t.sinks_per_lane, "warps_per_block": t.warps_per_block,
                 "blocks_per_sm": t.blocks_per_sm, "use_graph": t.use_graph,
-                "vjp_sinks_per_lane": t.vjp_sinks_per_lane}
+                "vjp_sinks_per_lane": t.vjp_sinks_per_lane, "source_tile": t.source_tile}
 
     def set_tuning(self, sinks_per_lane=None, warps_per_block=None, blocks_per_sm=None,
-                   use_graph=None, vjp_sinks_per_lane=None) -> None:
+                   use_graph=None, vjp_sinks_per_lane=None, source_tile=None) -> None:
         cur = self.tuning
         t = N.nf_tuning(cur["sinks_per_lane"] if sinks_per_lane is None else sinks_per_lane,
                         cur["warps_per_block"] if warps_per_block is None else warps_per_block,
                         cur["blocks_per_sm"] if blocks_per_sm is None else blocks_per_sm,
                         cur["use_graph"] if use_graph is None else int(use_graph),
-                        cur["vjp_sinks_per_lane"] if vjp_sinks_per_lane is None else vjp_sinks_per_lane)
+                        cur["vjp_sinks_per_lane"] if vjp_sinks_per_lane is None else vjp_sinks_per_lane,
+                        cur["source_tile"] if source_tile is None else source_tile)
         N.check(self._lib.nf_set_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_set_tuning")
 
     def autotune(self, reps: int = 2, cache: str | None = None) -> dict:
@@ -333,7 +335,7 @@ class NearField:
             hit = load_tuning_cache(cache).get(key)
             if hit:
                 self.set_tuning(**{k: hit[k] for k in ("sinks_per_lane", "warps_per_block",
-                                                       "blocks_per_sm") if k in hit})
+                                                       "blocks_per_sm", "source_tile") if k in hit})
                 return self.tuning
         t = N.nf_tuning()
         N.check(self._lib.nf_autotune(self._ctx, int(reps), ctypes.byref(t),

@@ -109,7 +109,7 @@ def test_binning_clustered_bit_exact(dev):
 
 
 # ---------------------------------------------------------------- forward
-@pytest.mark.parametrize("precision", ["fp32", "fp32_comp"])
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp", "fp32_comp_pair"])
 def test_tiny_forward_parity(dev, precision):
     box = synth.tiny()
     ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
@@ -133,11 +133,28 @@ def test_comp_is_not_less_accurate(dev):
     ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
     e32 = frac_err(gpu_accel(box, dev, "fp32")[0], ref)
     ec = frac_err(gpu_accel(box, dev, "fp32_comp")[0], ref)
+    ep = frac_err(gpu_accel(box, dev, "fp32_comp_pair")[0], ref)
     assert np.median(ec) <= np.median(e32) * 1.05
+    assert np.median(ep) <= np.median(ec) * 1.05
     assert_parity(gpu_accel(box, dev, "fp32")[0], ref)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp32_comp", "fp64"])
+def test_comp_on_dense_cells(dev):
+    """Clustered cells with thousands of sources per sink: the fold of many
+    tile sums is where the compensated total pays; both compensated forms
+    must be at least as accurate as plain FP32 there."""
+    pos, _ = synth.clustered_box(48 ** 3, 31, n_halos=12)
+    box = synth.Box("cl48", pos, 1.0, 13, (1 / 48) / 40, 1 / 48 ** 3)
+    idx = np.arange(0, box.n, 5)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm, sinks=idx)
+    errs = {p: frac_err(gpu_accel(box, dev, p)[0][idx], ref) for p in ("fp32", "fp32_comp", "fp32_comp_pair")}
+    for p, e in errs.items():
+        assert np.median(e) <= MED_TOL and np.quantile(e, 0.999) <= P999_TOL, p
+    assert np.median(errs["fp32_comp"]) <= np.median(errs["fp32"]) * 1.05
+    assert np.median(errs["fp32_comp_pair"]) <= np.median(errs["fp32"]) * 1.05
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_comp", "fp32_comp_pair", "fp64"])
 def test_unequal_masses(dev, precision):
     box = synth.tiny(seed=5)
     mass = np.random.default_rng(3).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
@@ -149,6 +166,21 @@ def test_unequal_masses(dev, precision):
         assert_parity(got, ref, what=precision)
     P = np.array(st["momentum"])
     assert np.all(np.abs(P) <= 1e-5 * st["abs_momentum"])
+
+
+@pytest.mark.parametrize("tile,K,precision", [(64, 4, "fp32"), (256, 4, "fp32"), (64, 1, "fp32_comp"),
+                                               (256, 2, "fp32_comp"), (256, 2, "fp32_comp_pair")])
+def test_source_tiles(dev, tile, K, precision):
+    """Every staged-tile size gives the same accelerations within the
+    tolerance, with equal and unequal masses."""
+    box = synth.early(n_side=40, cpd=11)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    got, _ = gpu_accel(box, dev, precision, sinks_per_lane=K, source_tile=tile)
+    assert_parity(got, ref, what=f"tile {tile} K={K} {precision}")
+    mass = np.random.default_rng(tile).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    refm = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    gotm, _ = gpu_accel(box, dev, precision, mass=mass, sinks_per_lane=K, source_tile=tile)
+    assert_parity(gotm, refm, what=f"tile {tile} masses")
 
 
 @pytest.mark.parametrize("K,warps", [(1, 2), (1, 4), (2, 4), (2, 8), (4, 4), (4, 16), (2, 16)])
@@ -279,6 +311,24 @@ def test_repeated_calls_with_new_outputs_and_rebin(dev):
     assert not np.array_equal(outs[0], outs[2])
 
 
+def test_host_buffer_path_with_pinned_buffers(dev):
+    """Page-locked host buffers (the end-to-end path's fast case) give the
+    device path's result, also on a second call that replays the graph."""
+    box = synth.tiny(seed=3)
+    nf = make_nf(box, dev)
+    hpos = torch.from_numpy(box.pos).pin_memory().numpy()
+    hacc = torch.full((box.n, 3), float("nan"), dtype=torch.float32).pin_memory().numpy()
+    nf.accel_host(hpos, gm=box.gm, out=hacc)
+    a1 = hacc.copy()
+    nf.accel_host(hpos, gm=box.gm, out=hacc)            # graph replay into the same buffer
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    a_dev = nf.accel().cpu().numpy()
+    st = nf.stats()
+    nf.close()
+    assert np.array_equal(a1, a_dev) and np.array_equal(hacc, a_dev)
+    assert np.all(np.abs(np.array(st["momentum"])) <= 1e-5 * st["abs_momentum"])
+
+
 def test_host_buffer_path_matches_device_path(dev):
     box = synth.tiny(seed=3)
     nf = make_nf(box, dev)
@@ -349,6 +399,7 @@ def test_autotune_picks_a_valid_shape(dev, tmp_path):
     cache = str(tmp_path / "tune.json")
     t = nf.autotune(reps=1, cache=cache)
     assert t["sinks_per_lane"] in (1, 2, 4) and t["warps_per_block"] in (4, 8)
+    assert t["source_tile"] in (64, 128, 256)
     ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
     assert_parity(nf.accel().cpu().numpy(), ref)
     nf.close()
