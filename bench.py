@@ -199,9 +199,17 @@ class ClockSampler:
                 "power_w_max": float(max(power)), "samples": len(sm), "reasons": sorted(reasons)}
 
 
+# --n-side / --cpd: a smaller box of the same recipe (for profiler captures
+# that must stay small); 0 keeps the workload's own size
+BOX_OVERRIDE = {}
+
+
 def make_workload(name: str):
     import synth
-    return synth.make(name)
+    kw = dict(BOX_OVERRIDE) if name in ("early", "late", "adjoint") else {}
+    if name == "late" and "n_side" in kw:       # the halo count scales with N, as for the other boxes
+        kw["n_halos"] = synth._scaled_halos(kw["n_side"] ** 3)
+    return synth.make(name, **kw)
 
 
 def host_cpu_model(cpuinfo: str = "/proc/cpuinfo") -> str:
@@ -396,9 +404,10 @@ class PlainRunner:
         eps = 2.5 * box.eps if self.law == "spline" else box.eps
         self.nf = NearField(box.L, box.cpd, eps, radius=box.R, precision=args.precision,
                             capacity=box.n, device=dev, softening=self.law)
-        if args.sinks_per_lane or args.warps:
+        if args.sinks_per_lane or args.warps or args.no_pencils:
             self.nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
-                               warps_per_block=args.warps or None)
+                               warps_per_block=args.warps or None,
+                               use_pencils=0 if args.no_pencils else None)
         self.passes = 1
         self.kde_b = 0.4 * box.L / box.n ** (1.0 / 3.0) if getattr(args, "kde", False) else None
         self.dens = torch.empty(box.n, dtype=torch.float32, device=dev) if self.kde_b else None
@@ -673,10 +682,11 @@ class BatchedRunner:
                             capacity=self.n, device=dev)
         self.singles = [NearField(b.L, b.cpd, b.eps, precision=args.precision, capacity=b.n, device=dev)
                         for b in self.boxes]
-        if args.sinks_per_lane or args.warps:
+        if args.sinks_per_lane or args.warps or args.no_pencils:
             for nf in [self.nf] + self.singles:
                 nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
-                              warps_per_block=args.warps or None)
+                              warps_per_block=args.warps or None,
+                              use_pencils=0 if args.no_pencils else None)
         self.passes = 1
         self.n_boxes_total = len(allb)
         self.gms = [b.gm for b in self.boxes]
@@ -1207,11 +1217,17 @@ def main(argv=None):
                     help="time full leapfrog steps (kick, drift, re-bin, accelerations, kick)")
     ap.add_argument("--sinks-per-lane", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--no-pencils", action="store_true",
+                    help="serve every cell with the per-warp items (no four-cell pencil blocks)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=0.0,
                     help="oracle seconds per step of the reference arm (default: 2-20 s, sized to the run)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-side", type=int, default=0,
+                    help="particles per side of the early, late or adjoint box (a smaller box of the "
+                         "same recipe, e.g. for profiler captures); 0 = the workload's own")
+    ap.add_argument("--cpd", type=int, default=0, help="cells per dimension with --n-side")
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="slab: split one box into x slabs over the ranks, ghost slabs swapped between "
                          "neighbours (with one rank, its own); replicas: every rank runs the whole workload")
@@ -1222,6 +1238,10 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.n_side:
+        BOX_OVERRIDE["n_side"] = args.n_side
+    if args.cpd:
+        BOX_OVERRIDE["cpd"] = args.cpd
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

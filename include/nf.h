@@ -97,6 +97,7 @@ typedef struct nf_stats {
                                 replays counted kernel by kernel */
     double  far_ms;          /* device time of the last nf_compute_far (0 if none) */
     double  far_conv_ms;     /* of which the per-frequency tensor products */
+    int64_t n_pencils;       /* pencils (four-cell runs served by one block) of the last compute */
 } nf_stats;
 
 /* Launch shape of the pair kernels. sinks_per_lane in {1,2,4}; warps_per_block
@@ -104,7 +105,10 @@ typedef struct nf_stats {
  * replays the compute phase from a captured CUDA graph; source_tile in
  * {0, 64, 128, 256}: sources staged in shared memory per tile by the plain
  * (Plummer, no density) FP32 kernels, 0 meaning 128 (the other kernels
- * always stage 128). */
+ * always stage 128); use_pencils = 1 lets the plain FP32 forward pass
+ * (sinks_per_lane 4, R <= 2) serve runs of four z-adjacent cells with one
+ * block whose warps share the staged sources (the first 64 sinks of each
+ * cell; where the neighbourhood is sparse enough), the rest as usual. */
 typedef struct nf_tuning {
     int sinks_per_lane;
     int warps_per_block;
@@ -112,6 +116,7 @@ typedef struct nf_tuning {
     int use_graph;
     int vjp_sinks_per_lane;   /* sinks per lane of the adjoint kernel; 0 = as sinks_per_lane */
     int source_tile;
+    int use_pencils;
 } nf_tuning;
 
 /*

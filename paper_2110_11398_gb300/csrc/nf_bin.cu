@@ -289,9 +289,8 @@ __global__ void __launch_bounds__(kKeyThreads) k_cell_keys(const float *__restri
                 bad = bad || !ok;
                 cid[i] = cell;
             }
-            // a warp's particles often share the high digits (input order is
-            // often spatially coherent): then one add counts them all, else
-            // the lanes of each digit are counted by one add
+            // the digit histograms of every pass: the lanes of one digit are
+            // counted by one add
             const unsigned live_mask = __ballot_sync(0xffffffffu, live);
             if (live_mask) {
                 for (int p = 0; p < passes; ++p) {

@@ -60,6 +60,8 @@ struct Ctx {
     // work list
     int *nsrc_cell = nullptr;                      // [n_cells]
     WorkItem *items = nullptr;                     // [capacity]
+    int *pencils = nullptr;                        // [n_cells / kPencil + 1] first cell of each pencil item
+    unsigned char *pencil_ok = nullptr;            // [n_cells] at a pencil's first cell: served as a pencil
     Decomp *decomp_d = nullptr;                    // [3]: tables for K = 1, 2, 4
     int decomp_built = 0;                          // bit i: table i uploaded
     int decomp_k = 0;                              // K of the next work list

@@ -14,6 +14,15 @@ constexpr int kMaxRadius = 3;
 constexpr int kMaxNbr = (2 * kMaxRadius + 1) * (2 * kMaxRadius + 1) * (2 * kMaxRadius + 1);
 // Sources staged per warp tile.
 constexpr int kTile = 128;
+// Pencils (k_pencils): kPencil z-consecutive cells of one (x, y) row served
+// by one block of kPencil warps that share every staged column of sources;
+// each warp takes the first kPencilSinks sinks of its cell (the rest make
+// ordinary items), and a column (the pencil's cells plus R on either side in
+// z, at one (dx, dy)) holds at most kColMax sources (odd counts padded to
+// even).
+constexpr int kPencil = 4;
+constexpr int kPencilSinks = 64;
+constexpr int kColMax = 768;
 // Number of cost buckets of the work list (heaviest items are served first).
 constexpr int kBuckets = 64;
 // Max items one remainder of a cell can be cut into (see make_decomp()).
@@ -65,19 +74,18 @@ struct BoxDev {
     double gm_d;       // same G m, double
     int slab_x0;       // slab contexts: first owned x slab (global index)
     int slab_nx;       // slab contexts: owned x slabs; 0 for a whole periodic box
+    // x index map of neighbour rows (xwrap): t + (t < 0 ? x_lo_add : 0) +
+    // (t >= x_hi ? x_hi_add : 0). A whole box wraps periodically (CPD, CPD,
+    // -CPD). A slab context keeps its owned slabs at local x 0..nx-1, then the
+    // R ghost slabs on its left (global x0-R..x0-1) at nx..nx+R-1 and the R on
+    // its right (global x0+nx..x0+nx+R-1) at nx+R..nx+2R-1 (nx+R, nx, R), so
+    // an owned sink's neighbours never wrap.
+    int x_lo_add, x_hi, x_hi_add;
 };
 
-// x index of the cell row at offset dx from local x slab cx. A whole box
-// wraps periodically. A slab context keeps its owned slabs at local x
-// 0..nx-1, then the R ghost slabs on its left (global x0-R..x0-1) at
-// nx..nx+R-1 and the R on its right (global x0+nx..x0+nx+R-1) at
-// nx+R..nx+2R-1, so an owned sink's neighbours never wrap.
-__host__ __device__ __forceinline__ int nbr_slab(const BoxDev &B, int cx, int dx, int R) {
-    const int t = cx + dx;
-    if (B.slab_nx == 0) return t < 0 ? t + B.cpd : (t >= B.cpd ? t - B.cpd : t);
-    if (t < 0) return B.slab_nx + R + t;
-    if (t >= B.slab_nx) return B.slab_nx + R + (t - B.slab_nx);
-    return t;
+// Local x index of the cell row at x offset t (owned/sink x plus dx).
+__device__ __forceinline__ int xwrap(const BoxDev &B, int t) {
+    return t + (t < 0 ? B.x_lo_add : 0) + (t >= B.x_hi ? B.x_hi_add : 0);
 }
 
 // One unit of pair work: `n` consecutive cell-sorted sinks of one cell,
@@ -97,6 +105,8 @@ struct DevState {
     int queue_head;              // persistent-kernel work counter
     int max_occ;                 // largest cell population
     unsigned long long interactions;
+    int n_pencils;               // pencil items of the last work-list build
+    int pencil_head;             // pencil kernel work counter
     int bucket_count[kBuckets];
     int bucket_cursor[kBuckets];
 };
@@ -182,7 +192,8 @@ namespace nf {
 struct Ctx;
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
                        cudaStream_t s);
-cudaError_t launch_worklist(Ctx *c, cudaStream_t s);
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils = false);
+bool pencils_active(const Ctx *c, const nf_tuning &t, bool density);
 cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s,
                          float *dens = nullptr);
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);

@@ -39,7 +39,7 @@ __device__ __forceinline__ int cell_nsrc(const BoxDev &B, int local, const int *
     const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
     int s = 0;
     for (int dx = -R; dx <= R; ++dx) {
-        const int x = nbr_slab(B, cx, dx, R);
+        const int x = xwrap(B, cx + dx);
         for (int dy = -R; dy <= R; ++dy) {
             const int row = B.cell_off + (x * cpd + wrapc(cy + dy, cpd)) * cpd;
             for (int dz = -R; dz <= R; ++dz) s += count[row + wrapc(cz + dz, cpd)];
@@ -69,7 +69,51 @@ struct WLArgs {
     const Decomp *decomp;
     DevState *st;
     WorkItem *items;
+    int pencils_on;            // serve eligible pencils with k_pencils
+    unsigned char *pencil_ok;  // [n_cells]: at a pencil's first cell, 1 if it is served as a pencil
+    int *pencils;              // pencil items: first cell of each
 };
+
+// Cell c's pencil is served by k_pencils (its cells make no other items).
+__device__ __forceinline__ bool cell_in_pencil(const WLArgs &a, const BoxDev &B, int64_t c) {
+    if (!a.pencils_on) return false;
+    const int cz = ((int)c - B.cell_off) % B.cpd;
+    if (cz >= (B.cpd / kPencil) * kPencil) return false;
+    return a.pencil_ok[c - cz % kPencil] != 0;
+}
+
+// Pencil items: a thread per pencil's first cell decides whether the pencil
+// is served by k_pencils (every staged column fits kColMax, at least one
+// cell is not empty) and, if so, appends it to the pencil list. k_pencils
+// takes the first kPencilSinks sinks of each of the pencil's cells; the
+// rest of a fuller cell makes ordinary items.
+__global__ void __launch_bounds__(256) k_wl_pencils(WLArgs a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_cells) return;
+    const int box = a.n_boxes == 1 ? 0 : box_of_cell(a.boxes, a.n_boxes, (int)c);
+    const BoxDev &B = a.boxes[box];
+    const int cpd = B.cpd, R = a.R, W = 2 * R + 1;
+    const int local = (int)c - B.cell_off;
+    const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
+    if (cz % kPencil != 0 || cz >= (cpd / kPencil) * kPencil) return;
+    bool ok = true, any = false;
+    for (int j = 0; j < kPencil; ++j) any = any || a.count[c + j] > 0;
+    for (int ix = 0; ix < W && ok; ++ix) {
+        const int x = xwrap(B, cx + ix - R);
+        for (int iy = 0; iy < W && ok; ++iy) {
+            const int row = B.cell_off + (x * cpd + wrapc(cy + iy - R, cpd)) * cpd;
+            int tot = 0;
+            for (int k = 0; k < kPencil + 2 * R; ++k) {
+                const int n = a.count[row + wrapc(cz - R + k, cpd)];
+                tot += n + (n & 1);
+            }
+            ok = tot <= kColMax;
+        }
+    }
+    ok = ok && any;
+    a.pencil_ok[c] = ok ? 1 : 0;
+    if (ok) a.pencils[atomicAdd(&a.st->n_pencils, 1)] = (int)c;
+}
 
 __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
     __shared__ int hist[kBuckets];
@@ -90,12 +134,16 @@ __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
             a.nsrc_cell[c] = ns;
             inter = (unsigned long long)n * (unsigned long long)ns;
             mx = n;
-            const int full = 32 * a.K;
-            const int q = n / full, r = n % full;
-            if (q) atomicAdd(&hist[cost_bucket(ns, a.K, 0)], q);
-            for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
-                const int ent = a.decomp->entry[r][e];
-                atomicAdd(&hist[cost_bucket(ns, a.K, ent & 0xff)], 1);
+            // sinks beyond the first kPencilSinks of a pencil cell make items
+            const int ni = cell_in_pencil(a, B, c) ? max(0, n - kPencilSinks) : n;
+            if (ni > 0) {
+                const int full = 32 * a.K;
+                const int q = ni / full, r = ni % full;
+                if (q) atomicAdd(&hist[cost_bucket(ns, a.K, 0)], q);
+                for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
+                    const int ent = a.decomp->entry[r][e];
+                    atomicAdd(&hist[cost_bucket(ns, a.K, ent & 0xff)], 1);
+                }
             }
         }
     }
@@ -144,11 +192,16 @@ __global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
     __syncthreads();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = 0, ns = 0, box = 0;
+    int skip = 0;                       // leading sinks served by k_pencils
     if (c < a.n_cells) {
         n = a.count[c];
         if (n > 0) {
             box = a.n_boxes == 1 ? 0 : box_of_cell(a.boxes, a.n_boxes, (int)c);
             ns = a.nsrc_cell[c];
+            if (cell_in_pencil(a, a.boxes[box], c)) {
+                skip = min(n, kPencilSinks);
+                n -= skip;
+            }
         }
     }
     const int full = 32 * a.K;
@@ -165,7 +218,7 @@ __global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
     }
     __syncthreads();
     if (n > 0) {
-        const int first = a.cell_start[c];
+        const int first = a.cell_start[c] + skip;
         if (q) {
             const int b = cost_bucket(ns, a.K, 0);
             const int p = base[b] + atomicAdd(&cnt[b], q);
@@ -210,6 +263,7 @@ struct PairArgs {
     int nbr;                   // (2R+1)^3
     int tbl;                   // per-warp table stride (ints), >= nbr + 1
     float *dens;               // N, input order: kernel density estimate (KDE kernels)
+    int n_boxes;
 };
 
 // Per-warp neighbourhood table: pfx[ci] = exclusive prefix of the source
@@ -229,7 +283,7 @@ __device__ __forceinline__ int build_table(const PairArgs &a, const BoxDev &B, i
         if (ci < a.nbr) {
             const int ix = ci / (W * W), iy = (ci / W) % W, iz = ci % W;
             const int g = B.cell_off +
-                          (nbr_slab(B, cx, ix - R, R) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
+                          (xwrap(B, cx + ix - R) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
                           wrapc(cz + iz - R, cpd);
             st = a.cell_start[g];
             cnt = a.cell_start[g + 1] - st;
@@ -498,6 +552,194 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     o[1] = v[1] * sc;
                     o[2] = v[2] * sc;
                 }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ pencil kernel
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Forward pair kernel for pencils (plain FP32, Plummer, K = 4 sinks per
+// lane, two lanes per sink): one block of kPencil warps takes kPencil
+// z-consecutive cells cz0..cz0+3 of one (x, y) row, warp w the first
+// kPencilSinks sinks of cell cz0 + w. The block stages, for each of the (2R+1)^2 (dx, dy) columns, the
+// column's kPencil + 2R cells (z from cz0 - R) once; warp w sums over the
+// 2R+1 of them around its own cell, a contiguous range of the staged
+// column. Columns are copied with cp.async one ahead of the one being summed.
+// Coordinates are taken in the frame of the pencil's middle (cell
+// cz0 + 1.5 in z): sources shift by (dx, dy, k - R - 1.5), the sinks of warp
+// w by (0, 0, w - 1.5); all shifts are exact halves and the shifted values
+// stay below 4 cell units for R <= 2. Each cell's staged run is padded to an
+// even length with a far source (adds 0), so every warp's range starts on a
+// packed pair. The per-column sums are folded into the running totals.
+template <bool EQ>
+__global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int *__restrict__ pencils) {
+    constexpr int K = 4;
+    constexpr int MAXC = kPencil + 4;           // cells per column for R <= 2
+    constexpr int MAXCOL = 25;                  // (2R + 1)^2 for R <= 2
+    __shared__ __align__(16) float4 raw[2][kColMax];
+    __shared__ __align__(16) float soa[EQ ? 3 : 4][kColMax];
+    __shared__ int t_start[MAXCOL][MAXC];
+    __shared__ int t_cnt[MAXCOL][MAXC];
+    __shared__ int t_pfx[MAXCOL][MAXC + 1];
+    __shared__ int s_item;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int R = a.R, W = 2 * R + 1, ncol = W * W, ncell = kPencil + 2 * R;
+    const int g = lane >> 1, sp = lane & 1;
+    const int n_pen = a.st->n_pencils;
+    const f2_t *px = reinterpret_cast<const f2_t *>(soa[0]);
+    const f2_t *py = reinterpret_cast<const f2_t *>(soa[1]);
+    const f2_t *pz = reinterpret_cast<const f2_t *>(soa[2]);
+    const f2_t *pm = reinterpret_cast<const f2_t *>(soa[EQ ? 2 : 3]);
+    for (;;) {
+        __syncthreads();                        // the previous pencil is done with shared memory
+        if (tid == 0) s_item = atomicAdd(&a.st->pencil_head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_pen) break;
+        const int c0 = pencils[it];
+        const BoxDev *Bp = a.boxes + (a.n_boxes == 1 ? 0 : box_of_cell(a.boxes, a.n_boxes, c0));
+        const int cpd = Bp->cpd;
+        const int local = c0 - Bp->cell_off;
+        const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz0 = local % cpd;
+        // the staged columns: start and count of each cell
+        for (int e = tid; e < ncol * ncell; e += 32 * kPencil) {
+            const int col = e / ncell, k = e % ncell;
+            const int gc = Bp->cell_off +
+                           (xwrap(*Bp, cx + col / W - R) * cpd + wrapc(cy + col % W - R, cpd)) * cpd +
+                           wrapc(cz0 - R + k, cpd);
+            const int st = a.cell_start[gc];
+            t_start[col][k] = st;
+            t_cnt[col][k] = a.cell_start[gc + 1] - st;
+        }
+        __syncthreads();
+        if (tid < ncol) {                       // padded exclusive prefix of each column
+            int run = 0;
+            for (int k = 0; k < ncell; ++k) {
+                t_pfx[tid][k] = run;
+                run += t_cnt[tid][k] + (t_cnt[tid][k] & 1);
+            }
+            t_pfx[tid][ncell] = run;
+        }
+        __syncthreads();
+        // sinks of warp w: cell cz0 + w, the middle column's cell R + w
+        const int mid = R * W + R;
+        const int s0 = t_start[mid][R + w], ns = min(t_cnt[mid][R + w], kPencilSinks);
+        const f2_t eps2 = f2_pack(Bp->eps2, Bp->eps2);
+        const float zs = (float)w - 1.5f;
+        f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int si = g + 16 * k;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (si < ns) p = a.sorted[s0 + si];
+            const float z = p.z + zs;
+            xi[k] = f2_pack(p.x, p.x);
+            yi[k] = f2_pack(p.y, p.y);
+            zi[k] = f2_pack(z, z);
+            ax[k] = ay[k] = az[k] = 0ull;
+        }
+        // column 0 in flight
+        for (int k = 0; k < ncell; ++k) {
+            const int cnt = t_cnt[0][k], base = t_pfx[0][k], st = t_start[0][k];
+            for (int t = tid; t < cnt; t += 32 * kPencil) cp_async16(&raw[0][base + t], a.sorted + st + t);
+        }
+        cp_async_commit();
+        for (int col = 0; col < ncol; ++col) {
+            const int buf = col & 1;
+            cp_async_wait_all();
+            __syncthreads();                    // column col landed; the previous sums are done
+            if (col + 1 < ncol) {
+                for (int k = 0; k < ncell; ++k) {
+                    const int cnt = t_cnt[col + 1][k], base = t_pfx[col + 1][k], st = t_start[col + 1][k];
+                    for (int t = tid; t < cnt; t += 32 * kPencil)
+                        cp_async16(&raw[buf ^ 1][base + t], a.sorted + st + t);
+                }
+            }
+            cp_async_commit();
+            // shift into the pencil's frame, structure of arrays, pad odd cells
+            const float ox = (float)(col / W - R), oy = (float)(col % W - R);
+            for (int k = 0; k < ncell; ++k) {
+                const int cnt = t_cnt[col][k], base = t_pfx[col][k];
+                const float oz = (float)(k - R) - 1.5f;
+                for (int t = tid; t < cnt + (cnt & 1); t += 32 * kPencil) {
+                    if (t < cnt) {
+                        const float4 p = raw[buf][base + t];
+                        soa[0][base + t] = p.x + ox;
+                        soa[1][base + t] = p.y + oy;
+                        soa[2][base + t] = p.z + oz;
+                        if (!EQ) soa[3][base + t] = p.w;
+                    } else {
+                        soa[0][base + t] = kFarAway;
+                        soa[1][base + t] = 0.f;
+                        soa[2][base + t] = 0.f;
+                        if (!EQ) soa[3][base + t] = 0.f;
+                    }
+                }
+            }
+            __syncthreads();
+            // warp w: cells w .. w + 2R of the column
+            const int lo = t_pfx[col][w] >> 1, npair = (t_pfx[col][w + W] >> 1) - lo;
+            f2_t tx[K], ty[K], tz[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
+            const int n_it = (npair - sp + 1) >> 1;
+#pragma unroll 2
+            for (int i2 = 0; i2 < n_it; ++i2) {
+                const int pp = lo + sp + 2 * i2;
+                const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];
+                f2_t m2 = 0ull;
+                if (!EQ) m2 = pm[pp];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const f2_t dx = f2_sub(x2, xi[k]);
+                    const f2_t dy = f2_sub(y2, yi[k]);
+                    const f2_t dz = f2_sub(z2, zi[k]);
+                    f2_t s2 = f2_fma(dx, dx, eps2);
+                    s2 = f2_fma(dy, dy, s2);
+                    s2 = f2_fma(dz, dz, s2);
+                    const f2_t r = f2_rsqrt(s2);
+                    f2_t f = f2_mul(f2_mul(r, r), r);
+                    if (!EQ) f = f2_mul(f, m2);
+                    tx[k] = f2_fma(f, dx, tx[k]);
+                    ty[k] = f2_fma(f, dy, ty[k]);
+                    tz[k] = f2_fma(f, dz, tz[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                ax[k] = f2_add(ax[k], tx[k]);
+                ay[k] = f2_add(ay[k], ty[k]);
+                az[k] = f2_add(az[k], tz[k]);
+            }
+        }
+        // epilogue: fold the packed halves, the two lanes of each sink, scale, un-permute
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const f2_t hs[3] = {ax[k], ay[k], az[k]};
+            float v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float h0, h1;
+                f2_unpack(hs[c], h0, h1);
+                float sum = h0 + h1;
+                sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+                v[c] = sum;
+            }
+            const int si = g + 16 * k;
+            if (sp == 0 && si < ns) {
+                const int i = a.perm[s0 + si];
+                const float sc = EQ ? __ldg(&Bp->gm) * __ldg(&Bp->inv_h2) : __ldg(&Bp->inv_h2);
+                float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+                o[0] = v[0] * sc;
+                o[1] = v[1] * sc;
+                o[2] = v[2] * sc;
             }
         }
     }
@@ -1018,6 +1260,7 @@ PairArgs make_args(Ctx *c, void *out, int out_f64) {
     a.nbr = (2 * c->R + 1) * (2 * c->R + 1) * (2 * c->R + 1);
     a.tbl = table_stride(c->R);
     a.dens = nullptr;
+    a.n_boxes = c->n_boxes;
     return a;
 }
 
@@ -1063,7 +1306,7 @@ void make_decomp(int K, Decomp *d) {
     }
 }
 
-cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils) {
     cudaError_t e;
     // reset counters (everything but the error word)
     if ((e = cudaMemsetAsync(&c->state->n_items, 0, sizeof(DevState) - sizeof(int), s))) return e;
@@ -1079,7 +1322,14 @@ cudaError_t launch_worklist(Ctx *c, cudaStream_t s) {
     a.decomp = c->decomp_d + (c->decomp_k == 1 ? 0 : (c->decomp_k == 2 ? 1 : 2));
     a.st = c->state;
     a.items = c->items;
+    a.pencils_on = pencils ? 1 : 0;
+    a.pencil_ok = c->pencil_ok;
+    a.pencils = c->pencils;
     const unsigned blocks = (unsigned)((c->n_sink_cells + 255) / 256 + (c->n_sink_cells == 0));
+    if (pencils) {
+        k_wl_pencils<<<blocks, 256, 0, s>>>(a);
+        c->launches += 1;
+    }
     k_wl_count<<<blocks, 256, 0, s>>>(a);
     k_wl_scan<<<1, 32, 0, s>>>(c->state);
     k_wl_write<<<blocks, 256, 0, s>>>(a);
@@ -1098,7 +1348,24 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
     if (!fn) return cudaErrorInvalidValue;
     PairArgs args = make_args(c, acc, out_f64);
     args.dens = dens;
-    return launch_generic(c, fn, 0, args, t, s, tile);
+    cudaError_t e = launch_generic(c, fn, 0, args, t, s, tile);
+    if (e || !pencils_active(c, t, dens == nullptr && !out_f64)) return e;
+    // the pencils, after the other items
+    void *pf = c->equal_mass ? fptr(k_pencils<true>) : fptr(k_pencils<false>);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pf, 32 * kPencil, 0))) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int *pens = c->pencils;
+    void *params[] = {&args, &pens};
+    c->launches += 1;
+    return cudaLaunchKernel(pf, dim3(c->sm_count * per_sm), dim3(32 * kPencil), params, 0, s);
+}
+
+// The pencil kernel serves the plain FP32 Plummer forward pass with FP32
+// output and no density, at K = 4 and R <= 2, when the tuning allows it.
+bool pencils_active(const Ctx *c, const nf_tuning &t, bool plain_out) {
+    return t.use_pencils && plain_out && c->precision == NF_PREC_FP32 &&
+           c->softening == NF_SOFT_PLUMMER && c->R <= 2 && t.sinks_per_lane == 4;
 }
 
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s) {

@@ -168,6 +168,34 @@ def test_unequal_masses(dev, precision):
     assert np.all(np.abs(P) <= 1e-5 * st["abs_momentum"])
 
 
+@pytest.mark.parametrize("box_kind", ["early", "clustered", "tiny"])
+def test_pencils_on_and_off(dev, box_kind):
+    """Four-cell pencils served by one block (sparse cells) against the
+    per-warp items alone: both within the tolerance, with equal and
+    unequal masses; on the near-uniform box most sinks go to pencils."""
+    if box_kind == "early":
+        box = synth.early(n_side=48, cpd=13)
+    elif box_kind == "clustered":
+        pos, _ = synth.clustered_box(48 ** 3, 9, n_halos=15)
+        box = synth.Box("cl48", pos, 1.0, 13, (1 / 48) / 40, 1 / 48 ** 3)
+    else:
+        box = synth.tiny(seed=6)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    on, st_on = gpu_accel(box, dev, use_pencils=1)
+    off, st_off = gpu_accel(box, dev, use_pencils=0)
+    assert_parity(on, ref, what=f"pencils {box_kind}")
+    assert_parity(off, ref, what=f"no pencils {box_kind}")
+    assert st_off["n_pencils"] == 0 and st_on["n_pencils"] > 0
+    assert st_on["interactions"] == st_off["interactions"]
+    if box_kind == "early":                 # every full pencil of the near-uniform box
+        assert st_on["n_pencils"] == box.cpd ** 2 * (box.cpd // 4)
+    mass = np.random.default_rng(3).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    refm = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    gotm, stm = gpu_accel(box, dev, mass=mass, use_pencils=1)
+    assert stm["n_pencils"] > 0
+    assert_parity(gotm, refm, what=f"pencils, masses {box_kind}")
+
+
 @pytest.mark.parametrize("tile,K,precision", [(64, 4, "fp32"), (256, 4, "fp32"), (64, 1, "fp32_comp"),
                                                (256, 2, "fp32_comp"), (256, 2, "fp32_comp_pair")])
 def test_source_tiles(dev, tile, K, precision):
