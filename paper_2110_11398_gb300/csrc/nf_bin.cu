@@ -16,8 +16,8 @@
 // coalesced. The digit histograms of every pass are counted once, in the
 // kernel that computes the cell ids. The last pass writes the cell-sorted
 // records (reading each particle's position at its input index) instead of
-// the sort values, so no separate gather pass is needed. Per-cell counts come
-// from the run boundaries of the sorted keys.
+// the sort values, so no separate gather pass is needed, and counts each
+// cell's particles from the runs of equal keys in its tile.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -333,6 +333,7 @@ struct SortArgs {
     int pow2;
     float4 *sorted;
     dbl4 *sorted_d;                // FP64 copy (FP64 reference contexts) or nullptr
+    int *count;                    // per-cell counts, zero on entry to the last pass
 };
 
 // Look-back word of (tile, digit): high 32 bits 2 * epoch (the tile's own
@@ -480,23 +481,16 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_pass(SortArgs a) {
             a.sorted[dest] = make_float4(rf[0], rf[1], rf[2], m);
             if (a.sorted_d) a.sorted_d[dest] = dbl4_make(rd[0], rd[1], rd[2], (double)m);
             a.vals_out[dest] = i;
-            a.keys_out[dest] = kk[u];
+            // per-cell counts: the tile's keys are in full key order here, so
+            // a cell's slots form one run; its last slot adds the run's end,
+            // its first subtracts the run's start (runs that continue in
+            // another tile add up across tiles)
+            const bool first = j == 0 || s_key[j - 1] != kk[u];
+            const bool last = j == tile_n - 1 || s_key[j + 1] != kk[u];
+            if (first && last) atomicAdd(&a.count[kk[u]], 1);
+            else if (first) atomicAdd(&a.count[kk[u]], -j);
+            else if (last) atomicAdd(&a.count[kk[u]], j + 1);
         }
-    }
-}
-
-// Per-cell counts from the runs of equal keys in the sorted key array: the
-// last element of a run adds its end, the first subtracts its start (each
-// cell gets one or two adds; count starts at zero).
-__global__ void k_cell_runs(const int *__restrict__ keys, int64_t n, int *__restrict__ count) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int c = keys[k];
-        const bool first = k == 0 || keys[k - 1] != c;
-        const bool last = k == n - 1 || keys[k + 1] != c;
-        if (first && last) count[c] = 1;
-        else if (first) atomicAdd(&count[c], -(int)k);
-        else if (last) atomicAdd(&count[c], (int)(k + 1));
     }
 }
 
@@ -599,7 +593,6 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
     if ((e = cudaMemsetAsync(&c->state->error, 0, sizeof(int), s))) return e;
     if (n == 0) {
         c->perm = c->vals_a;
-        c->sorted_keys = c->keys_a;
         return scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches);
     }
     const int passes = sort_passes(c->n_cells);
@@ -631,6 +624,7 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
     a.pow2 = c->pow2_all;
     a.sorted = c->sorted;
     a.sorted_d = c->precision == NF_PREC_FP64_REF ? c->sorted_d : nullptr;
+    a.count = c->count;
     for (int p = 0; p < passes; ++p) {
         const bool even = (p & 1) == 0;
         a.keys_in = even ? c->keys_a : c->keys_b;
@@ -647,11 +641,7 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
         if ((e = cudaGetLastError())) return e;
         c->launches += 1;
     }
-    c->sorted_keys = a.keys_out;
     c->perm = a.vals_out;
-    k_cell_runs<<<grid_for(n, 256, c->sm_count), 256, 0, s>>>(c->sorted_keys, n, c->count);
-    if ((e = cudaGetLastError())) return e;
-    c->launches += 1;
     return scan_exclusive(c->count, c->cell_start, c->n_cells, c->scan_tmp, s, &c->launches);
 }
 

@@ -45,7 +45,6 @@ struct Ctx {
     int *keys_a = nullptr, *keys_b = nullptr;     // [capacity]
     int *vals_a = nullptr, *vals_b = nullptr;     // [capacity]
     int *perm = nullptr;                           // alias of the final values buffer
-    int *sorted_keys = nullptr;                    // alias of the final keys buffer (cell ids, sorted)
     int *count = nullptr;                          // [n_cells]
     int *cell_start = nullptr;                     // [n_cells + 1]
     int *scan_tmp = nullptr;                       // block sums of the scans

@@ -572,19 +572,21 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // column's kPencil + 2R cells (z from cz0 - R) once; warp w sums over the
 // 2R+1 of them around its own cell, a contiguous range of the staged
 // column. Columns are copied with cp.async one ahead of the one being summed.
-// Coordinates are taken in the frame of the pencil's middle (cell
-// cz0 + 1.5 in z): sources shift by (dx, dy, k - R - 1.5), the sinks of warp
-// w by (0, 0, w - 1.5); all shifts are exact halves and the shifted values
-// stay below 4 cell units for R <= 2. Each cell's staged run is padded to an
-// even length with a far source (adds 0), so every warp's range starts on a
-// packed pair. The per-column sums are folded into the running totals.
+// Each source is staged in its sinks' cell frame as in k_pairs: x and y
+// shifted by (dx, dy), shared by the warps, and z once per warp, shifted by
+// that warp's cell offset k - R - w, so the pair arithmetic is k_pairs'
+// exactly. Each cell's staged run is padded to an even length with a far
+// source (adds 0), so every warp's range starts on a packed pair. The
+// per-column sums are folded into the running totals.
 template <bool EQ>
 __global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int *__restrict__ pencils) {
     constexpr int K = 4;
     constexpr int MAXC = kPencil + 4;           // cells per column for R <= 2
     constexpr int MAXCOL = 25;                  // (2R + 1)^2 for R <= 2
     __shared__ __align__(16) float4 raw[2][kColMax];
-    __shared__ __align__(16) float soa[EQ ? 3 : 4][kColMax];
+    __shared__ __align__(16) float sxy[2][kColMax];
+    __shared__ __align__(16) float szw[kPencil][kColMax];     // z in warp w's frame
+    __shared__ __align__(16) float sms[EQ ? 1 : kColMax];
     __shared__ int t_start[MAXCOL][MAXC];
     __shared__ int t_cnt[MAXCOL][MAXC];
     __shared__ int t_pfx[MAXCOL][MAXC + 1];
@@ -593,10 +595,10 @@ __global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int 
     const int R = a.R, W = 2 * R + 1, ncol = W * W, ncell = kPencil + 2 * R;
     const int g = lane >> 1, sp = lane & 1;
     const int n_pen = a.st->n_pencils;
-    const f2_t *px = reinterpret_cast<const f2_t *>(soa[0]);
-    const f2_t *py = reinterpret_cast<const f2_t *>(soa[1]);
-    const f2_t *pz = reinterpret_cast<const f2_t *>(soa[2]);
-    const f2_t *pm = reinterpret_cast<const f2_t *>(soa[EQ ? 2 : 3]);
+    const f2_t *px = reinterpret_cast<const f2_t *>(sxy[0]);
+    const f2_t *py = reinterpret_cast<const f2_t *>(sxy[1]);
+    const f2_t *pz = reinterpret_cast<const f2_t *>(szw[w]);
+    const f2_t *pm = reinterpret_cast<const f2_t *>(sms);
     for (;;) {
         __syncthreads();                        // the previous pencil is done with shared memory
         if (tid == 0) s_item = atomicAdd(&a.st->pencil_head, 1);
@@ -632,17 +634,15 @@ __global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int 
         const int mid = R * W + R;
         const int s0 = t_start[mid][R + w], ns = min(t_cnt[mid][R + w], kPencilSinks);
         const f2_t eps2 = f2_pack(Bp->eps2, Bp->eps2);
-        const float zs = (float)w - 1.5f;
         f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const int si = g + 16 * k;
             float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
             if (si < ns) p = a.sorted[s0 + si];
-            const float z = p.z + zs;
             xi[k] = f2_pack(p.x, p.x);
             yi[k] = f2_pack(p.y, p.y);
-            zi[k] = f2_pack(z, z);
+            zi[k] = f2_pack(p.z, p.z);
             ax[k] = ay[k] = az[k] = 0ull;
         }
         // column 0 in flight
@@ -663,23 +663,24 @@ __global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int 
                 }
             }
             cp_async_commit();
-            // shift into the pencil's frame, structure of arrays, pad odd cells
+            // shift into the sinks' frames, structure of arrays, pad odd cells
             const float ox = (float)(col / W - R), oy = (float)(col % W - R);
             for (int k = 0; k < ncell; ++k) {
                 const int cnt = t_cnt[col][k], base = t_pfx[col][k];
-                const float oz = (float)(k - R) - 1.5f;
                 for (int t = tid; t < cnt + (cnt & 1); t += 32 * kPencil) {
                     if (t < cnt) {
                         const float4 p = raw[buf][base + t];
-                        soa[0][base + t] = p.x + ox;
-                        soa[1][base + t] = p.y + oy;
-                        soa[2][base + t] = p.z + oz;
-                        if (!EQ) soa[3][base + t] = p.w;
+                        sxy[0][base + t] = p.x + ox;
+                        sxy[1][base + t] = p.y + oy;
+#pragma unroll
+                        for (int v = 0; v < kPencil; ++v) szw[v][base + t] = p.z + (float)(k - R - v);
+                        if (!EQ) sms[base + t] = p.w;
                     } else {
-                        soa[0][base + t] = kFarAway;
-                        soa[1][base + t] = 0.f;
-                        soa[2][base + t] = 0.f;
-                        if (!EQ) soa[3][base + t] = 0.f;
+                        sxy[0][base + t] = kFarAway;
+                        sxy[1][base + t] = 0.f;
+#pragma unroll
+                        for (int v = 0; v < kPencil; ++v) szw[v][base + t] = 0.f;
+                        if (!EQ) sms[base + t] = 0.f;
                     }
                 }
             }
