@@ -296,7 +296,11 @@ NF_API int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const fl
  * copies them back, then synchronises `stream`.
  *   pos_host   host [N x 3] float32 (pinned memory gives full copy speed)
  *   mass_host  host [N] float32 or NULL (then mass_if_null)
- *   acc_host   host [N x 3] float32 out
+ *   acc_host   host [N x 3] float32 out. If it is page-locked memory the
+ *              device can address (cudaHostAlloc / cudaHostRegister), the
+ *              pair kernels store the accelerations into it directly, so the
+ *              transfer overlaps the pass; otherwise they go to a device
+ *              buffer that is copied back after the pass.
  * Device staging buffers are allocated on first use and kept by the context.
  */
 NF_API int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, double mass_if_null,

@@ -169,6 +169,19 @@ cudaError_t split_copy(Ctx *c, void *dst, const void *src, size_t bytes, cudaMem
     return cudaSuccess;
 }
 
+// The device address of page-locked host memory (cudaHostAlloc, or
+// cudaHostRegister'ed) that the current device can store to, else nullptr
+// (pageable memory, device memory, unknown pointers).
+float *host_mapped(float *p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<float *>(at.devicePointer);
+}
+
 // The compute phase: work list, pair kernel, momentum diagnostic and the
 // copy of the counters to pinned host memory.
 cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nullptr) {
@@ -758,9 +771,13 @@ int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, do
     int rc = nf_bin_particles(ctx, c->st_pos, mass_host ? c->st_mass : nullptr, mass_if_null, n,
                               box_offsets, stream);
     if (rc) return rc;
-    rc = nf_compute_accel(ctx, c->st_acc, stream);
+    // Page-locked output the device can address: the pair kernels store each
+    // sink's acceleration there directly, so the transfer runs during the
+    // pass instead of after it. Any other host memory: device buffer + copy.
+    float *acc_dev = n > 0 ? host_mapped(acc_host) : nullptr;
+    rc = nf_compute_accel(ctx, acc_dev ? acc_dev : c->st_acc, stream);
     if (rc) return rc;
-    if (n > 0)
+    if (n > 0 && !acc_dev)
         NF_CK(c, split_copy(c, acc_host, c->st_acc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, s));
     NF_CK(c, cudaStreamSynchronize(s));
     return NF_OK;

@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(32 * kPencil) k_pencils(PairArgs a, const int 
 #pragma unroll
             for (int k = 0; k < K; ++k) tx[k] = ty[k] = tz[k] = 0ull;
             const int n_it = (npair - sp + 1) >> 1;
-#pragma unroll 2
+#pragma unroll 4
             for (int i2 = 0; i2 < n_it; ++i2) {
                 const int pp = lo + sp + 2 * i2;
                 const f2_t x2 = px[pp], y2 = py[pp], z2 = pz[pp];

@@ -340,21 +340,27 @@ def test_repeated_calls_with_new_outputs_and_rebin(dev):
 
 
 def test_host_buffer_path_with_pinned_buffers(dev):
-    """Page-locked host buffers (the end-to-end path's fast case) give the
-    device path's result, also on a second call that replays the graph."""
+    """Page-locked host buffers (the end-to-end path's fast case, where the
+    pair kernels store the accelerations into the host buffer directly) give
+    the device path's result, also on a second call that replays the graph,
+    and the momentum diagnostic reads the same accelerations."""
     box = synth.tiny(seed=3)
     nf = make_nf(box, dev)
     hpos = torch.from_numpy(box.pos).pin_memory().numpy()
     hacc = torch.full((box.n, 3), float("nan"), dtype=torch.float32).pin_memory().numpy()
     nf.accel_host(hpos, gm=box.gm, out=hacc)
     a1 = hacc.copy()
+    hacc[:] = np.nan
     nf.accel_host(hpos, gm=box.gm, out=hacc)            # graph replay into the same buffer
+    st_host = nf.stats()
     nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
     a_dev = nf.accel().cpu().numpy()
     st = nf.stats()
     nf.close()
     assert np.array_equal(a1, a_dev) and np.array_equal(hacc, a_dev)
     assert np.all(np.abs(np.array(st["momentum"])) <= 1e-5 * st["abs_momentum"])
+    assert st_host["abs_momentum"] == pytest.approx(st["abs_momentum"], rel=1e-12)
+    assert np.allclose(st_host["momentum"], st["momentum"], rtol=0, atol=1e-12 * st["abs_momentum"])
 
 
 def test_host_buffer_path_matches_device_path(dev):
