@@ -291,16 +291,17 @@ NF_API int nf_kdk_step(nf_ctx *ctx, float *pos, float *vel, float *acc, const fl
                        double mass_if_null, double dt, const int64_t *box_offsets, void *stream);
 
 /*
- * nf_accel_host -- end-to-end convenience call on HOST buffers: copies
- * positions (and masses) to the device, bins, computes the accelerations and
- * copies them back, then synchronises `stream`.
- *   pos_host   host [N x 3] float32 (pinned memory gives full copy speed)
- *   mass_host  host [N] float32 or NULL (then mass_if_null)
+ * nf_accel_host -- end-to-end convenience call on HOST buffers: positions
+ * (and masses) in, binning, accelerations out, then synchronises `stream`.
+ *   pos_host   host [N x 3] float32. If it is page-locked memory the device
+ *              can address (cudaHostAlloc / cudaHostRegister), the binning's
+ *              first kernel loads it directly and keeps a device copy for the
+ *              rest of the binning; otherwise it is copied to the device first.
+ *   mass_host  host [N] float32 or NULL (then mass_if_null); copied.
  *   acc_host   host [N x 3] float32 out. If it is page-locked memory the
- *              device can address (cudaHostAlloc / cudaHostRegister), the
- *              pair kernels store the accelerations into it directly, so the
- *              transfer overlaps the pass; otherwise they go to a device
- *              buffer that is copied back after the pass.
+ *              device can address, the pair kernels store the accelerations
+ *              into it directly, so the transfer overlaps the pass; otherwise
+ *              they go to a device buffer that is copied back after the pass.
  * Device staging buffers are allocated on first use and kept by the context.
  */
 NF_API int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, double mass_if_null,

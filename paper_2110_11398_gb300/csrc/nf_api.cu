@@ -170,16 +170,16 @@ cudaError_t split_copy(Ctx *c, void *dst, const void *src, size_t bytes, cudaMem
 }
 
 // The device address of page-locked host memory (cudaHostAlloc, or
-// cudaHostRegister'ed) that the current device can store to, else nullptr
-// (pageable memory, device memory, unknown pointers).
-float *host_mapped(float *p) {
+// cudaHostRegister'ed) that the current device can load from and store to,
+// else nullptr (pageable memory, device memory, unknown pointers).
+void *host_mapped(const void *p) {
     cudaPointerAttributes at{};
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
-    return static_cast<float *>(at.devicePointer);
+    return at.devicePointer;
 }
 
 // The compute phase: work list, pair kernel, momentum diagnostic and the
@@ -486,12 +486,12 @@ int nf_init_slab(nf_ctx **out, int device, double box_size, int cpd, int radius,
 
 void nf_free(nf_ctx *ctx) { release(reinterpret_cast<Ctx *>(ctx)); }
 
-int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double mass_if_null,
-                     int64_t n, const int64_t *box_offsets, void *stream) {
-    Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (!c) return fail(nullptr, NF_EINVAL, "nf_bin_particles: ctx is NULL");
-    DeviceGuard guard(c->device);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+namespace {
+// nf_bin_particles; with pos_copy (device [n x 3]) the positions may be
+// page-locked host memory: the key kernel reads them once and writes the
+// device copy that the rest of the binning reads.
+int bin_particles(Ctx *c, const float *pos, float *pos_copy, const float *mass, double mass_if_null,
+                  int64_t n, const int64_t *box_offsets, cudaStream_t s) {
     c->binned = 0;
     if (n < 0 || n > c->capacity) return fail(c, NF_EINVAL, "nf_bin_particles: n must be in [0, capacity]");
     if (n > 0 && !pos) return fail(c, NF_EINVAL, "nf_bin_particles: pos is NULL");
@@ -540,7 +540,7 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
         }
     }
     NF_CK(c, cudaEventRecord(c->ev_bin0, s));
-    cudaError_t e = nf::launch_bin(c, pos, mass, c->m0, n, s);
+    cudaError_t e = nf::launch_bin(c, pos, mass, c->m0, n, s, pos_copy);
     if (e) return cuda_fail(c, e, "nf_bin_particles");
     NF_CK(c, cudaEventRecord(c->ev_bin1, s));
     c->have_bin_time = 1;
@@ -558,6 +558,16 @@ int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double ma
     c->ghosts_ready = 0;
     c->n_ghost = 0;
     return NF_OK;
+}
+}  // namespace
+
+int nf_bin_particles(nf_ctx *ctx, const float *pos, const float *mass, double mass_if_null,
+                     int64_t n, const int64_t *box_offsets, void *stream) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return fail(nullptr, NF_EINVAL, "nf_bin_particles: ctx is NULL");
+    DeviceGuard guard(c->device);
+    return bin_particles(c, pos, nullptr, mass, mass_if_null, n, box_offsets,
+                         reinterpret_cast<cudaStream_t>(stream));
 }
 
 int nf_set_box_masses(nf_ctx *ctx, const double *gm) {
@@ -763,18 +773,22 @@ int nf_accel_host(nf_ctx *ctx, const float *pos_host, const float *mass_host, do
         if (e) { cudaGetLastError(); return fail(c, NF_ENOMEM, "nf_accel_host: staging allocation failed"); }
         c->st_cap = m;
     }
+    // Page-locked host buffers that the device can address are read and
+    // written by the kernels themselves: the binning's key kernel loads the
+    // positions once (and keeps a device copy for the sort's gather), and the
+    // pair kernels store each sink's acceleration into acc_host as the pass
+    // goes. Other host memory goes through device buffers and copies.
+    const float *pos_dev = n > 0 ? static_cast<const float *>(host_mapped(pos_host)) : nullptr;
+    float *acc_dev = n > 0 ? static_cast<float *>(host_mapped(acc_host)) : nullptr;
     if (n > 0) {
-        NF_CK(c, split_copy(c, c->st_pos, pos_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+        if (!pos_dev)
+            NF_CK(c, split_copy(c, c->st_pos, pos_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
         if (mass_host)
             NF_CK(c, cudaMemcpyAsync(c->st_mass, mass_host, sizeof(float) * n, cudaMemcpyHostToDevice, s));
     }
-    int rc = nf_bin_particles(ctx, c->st_pos, mass_host ? c->st_mass : nullptr, mass_if_null, n,
-                              box_offsets, stream);
+    int rc = bin_particles(c, pos_dev ? pos_dev : c->st_pos, pos_dev ? c->st_pos : nullptr,
+                           mass_host ? c->st_mass : nullptr, mass_if_null, n, box_offsets, s);
     if (rc) return rc;
-    // Page-locked output the device can address: the pair kernels store each
-    // sink's acceleration there directly, so the transfer runs during the
-    // pass instead of after it. Any other host memory: device buffer + copy.
-    float *acc_dev = n > 0 ? host_mapped(acc_host) : nullptr;
     rc = nf_compute_accel(ctx, acc_dev ? acc_dev : c->st_acc, stream);
     if (rc) return rc;
     if (n > 0 && !acc_dev)

@@ -253,11 +253,12 @@ constexpr int kKeyChunk = kKeyThreads * kKeyPer;        // 1024 particles, 12 KB
 // then added to the global counts). A block copies a chunk of 1024
 // positions into shared memory with coalesced 16-byte loads, then each
 // thread takes four particles from there.
+template <bool COPY>
 __global__ void __launch_bounds__(kKeyThreads) k_cell_keys(const float *__restrict__ pos, int64_t n,
                                                            const int64_t *__restrict__ poff, int n_boxes,
                                                            const BoxDev *__restrict__ boxes, int pow2,
                                                            int passes, int *__restrict__ cid, BinState *bs,
-                                                           DevState *st) {
+                                                           DevState *st, float *__restrict__ pos_copy) {
     __shared__ __align__(16) float sp[3 * kKeyChunk];
     __shared__ int h[kMaxSortPasses][kDigits];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -267,12 +268,22 @@ __global__ void __launch_bounds__(kKeyThreads) k_cell_keys(const float *__restri
         const int cnt = (int)min((int64_t)kKeyChunk, n - c0);
         const float *src = pos + 3 * c0;
         __syncthreads();                       // previous chunk consumed
-        if (cnt == kKeyChunk && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        float *dst = COPY ? pos_copy + 3 * c0 : nullptr;        // the device copy
+        if (cnt == kKeyChunk && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
             const float4 *s4 = reinterpret_cast<const float4 *>(src);
             float4 *d4 = reinterpret_cast<float4 *>(sp);
-            for (int t = tid; t < 3 * kKeyChunk / 4; t += kKeyThreads) d4[t] = s4[t];
+            float4 *c4 = reinterpret_cast<float4 *>(dst);
+            for (int t = tid; t < 3 * kKeyChunk / 4; t += kKeyThreads) {
+                const float4 v = s4[t];
+                d4[t] = v;
+                if (COPY) c4[t] = v;
+            }
         } else {
-            for (int t = tid; t < 3 * cnt; t += kKeyThreads) sp[t] = src[t];
+            for (int t = tid; t < 3 * cnt; t += kKeyThreads) {
+                const float v = src[t];
+                sp[t] = v;
+                if (COPY) dst[t] = v;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -586,7 +597,7 @@ int sort_passes(int64_t n_cells) {
 }
 
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
-                       cudaStream_t s) {
+                       cudaStream_t s, float *pos_copy) {
     (void)m0;
     cudaError_t e;
     if ((e = cudaMemsetAsync(c->count, 0, sizeof(int) * c->n_cells, s))) return e;
@@ -597,9 +608,14 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
     }
     const int passes = sort_passes(c->n_cells);
     if ((e = cudaMemsetAsync(c->bin_state, 0, sizeof(BinState), s))) return e;
-    k_cell_keys<<<grid_for(n, kKeyChunk, c->sm_count), kKeyThreads, 0, s>>>(
-        pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, passes, c->keys_a, c->bin_state,
-        c->state);
+    if (pos_copy)
+        k_cell_keys<true><<<grid_for(n, kKeyChunk, c->sm_count), kKeyThreads, 0, s>>>(
+            pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, passes, c->keys_a, c->bin_state,
+            c->state, pos_copy);
+    else
+        k_cell_keys<false><<<grid_for(n, kKeyChunk, c->sm_count), kKeyThreads, 0, s>>>(
+            pos, n, c->poff_d, c->n_boxes, c->boxes_d, c->pow2_all, passes, c->keys_a, c->bin_state,
+            c->state, nullptr);
     if ((e = cudaGetLastError())) return e;
     c->launches += 1;
     // look-back words are told apart by an epoch per pass; when the counter
@@ -616,7 +632,7 @@ cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, in
     a.status = c->sort_status;
     a.bs = c->bin_state;
     a.st = c->state;
-    a.pos = pos;
+    a.pos = pos_copy ? pos_copy : pos;       // the last pass gathers from device memory
     a.mass = mass;
     a.poff = c->poff_d;
     a.n_boxes = c->n_boxes;

@@ -190,8 +190,11 @@ __device__ __forceinline__ int box_of_cell(const BoxDev *boxes, int n_boxes, int
 // Host-side entry points of each translation unit (C++ linkage, internal).
 namespace nf {
 struct Ctx;
+// pos_copy (optional, device [n x 3]): the key kernel also writes the positions
+// there as it reads them (pos may then be page-locked host memory), and the
+// sort's gather reads the copy.
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
-                       cudaStream_t s);
+                       cudaStream_t s, float *pos_copy = nullptr);
 cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils = false);
 bool pencils_active(const Ctx *c, const nf_tuning &t, bool density);
 cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s,

@@ -363,6 +363,29 @@ def test_host_buffer_path_with_pinned_buffers(dev):
     assert np.allclose(st_host["momentum"], st["momentum"], rtol=0, atol=1e-12 * st["abs_momentum"])
 
 
+def test_host_buffer_path_pinned_ragged_and_unaligned(dev):
+    """Page-locked positions that the key kernel reads itself: a count that
+    is not a whole number of its 1024-particle chunks, rows that start 12
+    bytes into the page-locked block (not 16-byte aligned), and per-particle
+    masses; the result equals the device path's bit for bit."""
+    box = synth.tiny(seed=5)
+    n = box.n - 77
+    pos = box.pos[:n]
+    rng = np.random.default_rng(5)
+    mass = (rng.random(n, dtype=np.float32) + 0.5) / n
+    big = torch.zeros((n + 1, 3), dtype=torch.float32).pin_memory()
+    big[1:] = torch.from_numpy(pos)
+    hpos = big.numpy()[1:]
+    assert hpos.ctypes.data % 16 == 12
+    hacc = torch.full((n, 3), float("nan"), dtype=torch.float32).pin_memory().numpy()
+    nf = make_nf(box, dev)
+    nf.accel_host(hpos, mass, out=hacc)
+    nf.bin(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev))
+    a_dev = nf.accel().cpu().numpy()
+    nf.close()
+    assert np.array_equal(hacc, a_dev)
+
+
 def test_host_buffer_path_matches_device_path(dev):
     box = synth.tiny(seed=3)
     nf = make_nf(box, dev)
