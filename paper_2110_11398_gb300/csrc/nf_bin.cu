@@ -42,15 +42,6 @@ static_assert(kSortThreads == kDigits, "one thread per digit in the per-digit st
 // goes on; the host turns the flag into NF_ETIMEOUT.
 constexpr unsigned kSpinLimit = 1u << 22;
 
-__device__ __forceinline__ int box_of_particle(const int64_t *poff, int n_boxes, int64_t i) {
-    int lo = 0, hi = n_boxes - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (poff[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // u = (x * CPD) / L. When L is a power of two the division is exact and
 // equals multiplication by 1/L, which avoids the FP64 divide.
 __device__ __forceinline__ double cell_unit(double x, const BoxDev &B, bool pow2) {

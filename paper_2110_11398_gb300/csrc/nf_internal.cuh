@@ -176,6 +176,16 @@ __device__ __forceinline__ f2_t f2_rsqrt(f2_t v) {
     return f2_pack(rsqrt_hw(a), rsqrt_hw(b));
 }
 
+// The box of input particle i: the last b with poff[b] <= i.
+__device__ __forceinline__ int box_of_particle(const int64_t *poff, int n_boxes, int64_t i) {
+    int lo = 0, hi = n_boxes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (poff[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ int box_of_cell(const BoxDev *boxes, int n_boxes, int cell) {
     int lo = 0, hi = n_boxes - 1;
     while (lo < hi) {

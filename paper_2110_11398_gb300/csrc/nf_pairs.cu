@@ -1111,32 +1111,14 @@ __global__ void k_gather_w(const float *__restrict__ w, int64_t n, const int *__
     }
 }
 
-// a10: FP64 momentum diagnostic, P = sum_i m_i a_i (FP64 sums) and the scale
-// sum_i m_i |a_i|, two-level fixed-order reduction (deterministic).
-__global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sorted,
-                                                  const int *__restrict__ perm, const void *acc,
-                                                  int f64, int64_t n, double *partial) {
-    double s[4] = {0, 0, 0, 0};
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = perm[k];
-        const double m = sorted[k].w;
-        double v[3];
-        if (f64) {
-            const double *p = reinterpret_cast<const double *>(acc) + 3 * i;
-            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
-        } else {
-            const float *p = reinterpret_cast<const float *>(acc) + 3 * i;
-            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
-        }
-        s[0] += m * v[0];
-        s[1] += m * v[1];
-        s[2] += m * v[2];
-        // |a| only scales the check: an FP32 magnitude avoids an FP64 square
-        // root per particle (FP64 throughput is low on this GPU)
-        const float a2 = (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        s[3] += m * (double)sqrtf(a2);
-    }
+// |a|^2 of a float32 acceleration for the momentum scale: the squares and
+// the two sums each rounded to float32, in this order (no contraction).
+__device__ __forceinline__ float mom_a2(float x, float y, float z) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z));
+}
+
+// Warp, then block, reduction of s[0..3] into partial[4 * blockIdx.x + c].
+__device__ __forceinline__ void mom_block_sum(double s[4], double *partial) {
     __shared__ double red[8][4];
     for (int c = 0; c < 4; ++c) {
         double x = s[c];
@@ -1151,11 +1133,86 @@ __global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sor
     }
 }
 
-__global__ void k_momentum_final(const double *partial, int nb, double *out) {
+// a10: FP64 momentum diagnostic, P = sum_i m_i a_i (FP64 sums; a product of
+// two floats is exact in FP64) and the scale S = sum_i m_i |a_i| (|a_i| a
+// float32 magnitude: it only scales the check), two-level fixed-order
+// reduction (deterministic). Per-particle masses: sinks in sorted order,
+// m_i from the records, a_i gathered through the permutation.
+__global__ void __launch_bounds__(256) k_momentum(const float4 *__restrict__ sorted,
+                                                  const int *__restrict__ perm, const void *acc,
+                                                  int f64, int64_t n, double *partial) {
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        const double m = sorted[k].w;
+        double v[3];
+        float a2;
+        if (f64) {
+            const double *p = reinterpret_cast<const double *>(acc) + 3 * i;
+            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
+            a2 = (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        } else {
+            const float *p = reinterpret_cast<const float *>(acc) + 3 * i;
+            const float x = p[0], y = p[1], z = p[2];
+            v[0] = x; v[1] = y; v[2] = z;
+            a2 = mom_a2(x, y, z);
+        }
+        s[0] += m * v[0];
+        s[1] += m * v[1];
+        s[2] += m * v[2];
+        s[3] += m * (double)sqrtf(a2);
+    }
+    mom_block_sum(s, partial);
+}
+
+// The same for equal masses (one G m per box): particles in input order, so
+// the accelerations are read contiguously and neither the records nor the
+// permutation are needed. One box (MULTI false): the sums of a_i and |a_i|,
+// scaled by G m in the final kernel; several boxes: each term takes its
+// box's G m.
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_momentum_eq(const void *acc, int f64, int64_t n,
+                                                     const int64_t *__restrict__ poff, int n_boxes,
+                                                     const BoxDev *__restrict__ boxes, double *partial) {
+    double s[4] = {0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v[3];
+        float a2;
+        if (f64) {
+            const double *p = reinterpret_cast<const double *>(acc) + 3 * i;
+            v[0] = p[0]; v[1] = p[1]; v[2] = p[2];
+            a2 = (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        } else {
+            const float *p = reinterpret_cast<const float *>(acc) + 3 * i;
+            const float x = p[0], y = p[1], z = p[2];
+            v[0] = x; v[1] = y; v[2] = z;
+            a2 = mom_a2(x, y, z);
+        }
+        const double r = (double)sqrtf(a2);
+        if (MULTI) {
+            const double m = boxes[box_of_particle(poff, n_boxes, i)].gm_d;
+            s[0] += m * v[0];
+            s[1] += m * v[1];
+            s[2] += m * v[2];
+            s[3] += m * r;
+        } else {
+            s[0] += v[0];
+            s[1] += v[1];
+            s[2] += v[2];
+            s[3] += r;
+        }
+    }
+    mom_block_sum(s, partial);
+}
+
+__global__ void k_momentum_final(const double *partial, int nb, const BoxDev *boxes, int scale_by_gm,
+                                 double *out) {
     if (threadIdx.x < 4) {
         double x = 0;
         for (int b = 0; b < nb; ++b) x += partial[4 * b + threadIdx.x];
-        out[threadIdx.x] = x;
+        out[threadIdx.x] = scale_by_gm ? boxes[0].gm_d * x : x;
     }
 }
 
@@ -1386,8 +1443,17 @@ cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, 
 }
 
 cudaError_t launch_momentum(Ctx *c, const void *acc, int acc_f64, cudaStream_t s) {
-    k_momentum<<<kMomBlocks, 256, 0, s>>>(c->sorted, c->perm, acc, acc_f64, c->n, c->mom_partial);
-    k_momentum_final<<<1, 32, 0, s>>>(c->mom_partial, kMomBlocks, c->mom_result);
+    const bool one_box = c->n_boxes == 1;
+    if (!c->equal_mass)
+        k_momentum<<<kMomBlocks, 256, 0, s>>>(c->sorted, c->perm, acc, acc_f64, c->n, c->mom_partial);
+    else if (one_box)
+        k_momentum_eq<false><<<kMomBlocks, 256, 0, s>>>(acc, acc_f64, c->n, c->poff_d, c->n_boxes,
+                                                        c->boxes_d, c->mom_partial);
+    else
+        k_momentum_eq<true><<<kMomBlocks, 256, 0, s>>>(acc, acc_f64, c->n, c->poff_d, c->n_boxes,
+                                                       c->boxes_d, c->mom_partial);
+    k_momentum_final<<<1, 32, 0, s>>>(c->mom_partial, kMomBlocks, c->boxes_d, c->equal_mass && one_box,
+                                      c->mom_result);
     c->launches += 2;
     return cudaGetLastError();
 }

@@ -4,16 +4,19 @@ Newton's third law makes the near-field force of a pair antisymmetric, so
 P = sum_i m_i a_i vanishes up to rounding (Maksimova et al. 2021, Sec. 3.1:
 every pair within the near-field radius is summed from both ends). The
 library reduces P, and the scale S = sum_i m_i |a_i|, on the GPU in FP64
-(k_momentum, a two-level fixed-order reduction). These tests recompute both
-on the host from the accelerations the library returned and the masses it
-binned, and require agreement to 1e-12 of S:
+(k_momentum / k_momentum_eq, a two-level fixed-order reduction). These tests
+recompute both on the host from the accelerations the library returned and
+the masses it binned, and require agreement to 1e-12 of S:
 
   - both sides sum the same FP64 terms m_i a_i (a product of two floats is
     exact in FP64), in different orders, so they differ by summation
-    rounding only: about sqrt(N) 1e-16 S;
-  - |a_i| is formed the same way on both sides: the FP64 sum of the exact
-    squares, rounded once to float32, then a correctly rounded float32
-    square root.
+    rounding only: about sqrt(N) 1e-16 S; with one mass for the whole box
+    the GPU sums a_i and multiplies by G m once, which differs from the
+    per-term products by rounding of the same size;
+  - |a_i| is formed the same way on both sides: for float32 accelerations
+    the float32 sum (x^2 + y^2) + z^2 of the float32 squares, each step
+    rounded, for float64 ones the FP64 sum of squares rounded once to
+    float32; then a correctly rounded float32 square root.
 
 A reduction that dropped one of its 512 block partials would move S by
 about 1/512 of itself and P by the sum of about N/512 terms that do not
@@ -45,7 +48,12 @@ def host_momentum(acc, mass):
     a = np.asarray(acc, np.float64)
     m = np.asarray(mass, np.float32).astype(np.float64)
     P = np.sum(m[:, None] * a, axis=0)
-    a2 = np.sum(a * a, axis=1).astype(np.float32)
+    if acc.dtype == np.float32:
+        x, y, z = acc[:, 0], acc[:, 1], acc[:, 2]
+        a2 = (x * x + y * y) + z * z                 # float32 operations
+    else:
+        a2 = np.sum(a * a, axis=1).astype(np.float32)
+    assert a2.dtype == np.float32
     S = float(np.sum(m * np.sqrt(a2).astype(np.float64)))
     return P, S
 
