@@ -410,10 +410,11 @@ class PlainRunner:
         eps = 2.5 * box.eps if self.law == "spline" else box.eps
         self.nf = NearField(box.L, box.cpd, eps, radius=box.R, precision=args.precision,
                             capacity=box.n, device=dev, softening=self.law)
-        if args.sinks_per_lane or args.warps or args.no_pencils:
+        if args.sinks_per_lane or args.warps or args.no_pencils or args.no_small_items:
             self.nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
                                warps_per_block=args.warps or None,
-                               use_pencils=0 if args.no_pencils else None)
+                               use_pencils=0 if args.no_pencils else None,
+                               small_items=0 if args.no_small_items else None)
         self.passes = 1
         self.kde_b = 0.4 * box.L / box.n ** (1.0 / 3.0) if getattr(args, "kde", False) else None
         self.dens = torch.empty(box.n, dtype=torch.float32, device=dev) if self.kde_b else None
@@ -688,11 +689,12 @@ class BatchedRunner:
                             capacity=self.n, device=dev)
         self.singles = [NearField(b.L, b.cpd, b.eps, precision=args.precision, capacity=b.n, device=dev)
                         for b in self.boxes]
-        if args.sinks_per_lane or args.warps or args.no_pencils:
+        if args.sinks_per_lane or args.warps or args.no_pencils or args.no_small_items:
             for nf in [self.nf] + self.singles:
                 nf.set_tuning(sinks_per_lane=args.sinks_per_lane or None,
                               warps_per_block=args.warps or None,
-                              use_pencils=0 if args.no_pencils else None)
+                              use_pencils=0 if args.no_pencils else None,
+                              small_items=0 if args.no_small_items else None)
         self.passes = 1
         self.n_boxes_total = len(allb)
         self.gms = [b.gm for b in self.boxes]
@@ -1227,6 +1229,8 @@ def main(argv=None):
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--no-pencils", action="store_true",
                     help="serve every cell with the per-warp items (no four-cell pencil blocks)")
+    ap.add_argument("--no-small-items", action="store_true",
+                    help="serve the items of at most 8 sinks with the tiled kernel too")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=0.0,
                     help="oracle seconds per step of the reference arm (default: 2-20 s, sized to the run)")

@@ -98,6 +98,7 @@ typedef struct nf_stats {
     double  far_ms;          /* device time of the last nf_compute_far (0 if none) */
     double  far_conv_ms;     /* of which the per-frequency tensor products */
     int64_t n_pencils;       /* pencils (four-cell runs served by one block) of the last compute */
+    int64_t n_small;         /* work items of the last compute served by the small-item kernel */
 } nf_stats;
 
 /* Launch shape of the pair kernels. sinks_per_lane in {1,2,4}; warps_per_block
@@ -108,7 +109,11 @@ typedef struct nf_stats {
  * always stage 128); use_pencils = 1 lets the plain FP32 forward pass
  * (sinks_per_lane 4, R <= 2) serve runs of four z-adjacent cells with one
  * block whose warps share the staged sources (the first 64 sinks of each
- * cell; where the neighbourhood is sparse enough), the rest as usual. */
+ * cell; where the neighbourhood is sparse enough), the rest as usual;
+ * small_items = 1 lets the same pass (sinks_per_lane 4) serve the work items
+ * of at most 8 sinks, mostly the sinks a cell has left after its full
+ * groups, with a kernel whose lanes read their sources straight from the
+ * records instead of staging tiles of the whole neighbourhood. */
 typedef struct nf_tuning {
     int sinks_per_lane;
     int warps_per_block;
@@ -117,6 +122,7 @@ typedef struct nf_tuning {
     int vjp_sinks_per_lane;   /* sinks per lane of the adjoint kernel; 0 = as sinks_per_lane */
     int source_tile;
     int use_pencils;
+    int small_items;
 } nf_tuning;
 
 /*

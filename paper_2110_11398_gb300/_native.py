@@ -36,14 +36,14 @@ class nf_stats(ctypes.Structure):
                 ("abs_momentum", ctypes.c_double), ("bin_ms", ctypes.c_double),
                 ("pair_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("far_ms", ctypes.c_double), ("far_conv_ms", ctypes.c_double),
-                ("n_pencils", ctypes.c_int64)]
+                ("n_pencils", ctypes.c_int64), ("n_small", ctypes.c_int64)]
 
 
 class nf_tuning(ctypes.Structure):
     _fields_ = [("sinks_per_lane", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("vjp_sinks_per_lane", ctypes.c_int), ("source_tile", ctypes.c_int),
-                ("use_pencils", ctypes.c_int)]
+                ("use_pencils", ctypes.c_int), ("small_items", ctypes.c_int)]
 
 
 class NFError(RuntimeError):

@@ -102,7 +102,8 @@ bool valid_tuning(const nf_tuning &t) {
     const int k = t.sinks_per_lane, w = t.warps_per_block, kv = t.vjp_sinks_per_lane, st = t.source_tile;
     return (k == 1 || k == 2 || k == 4) && (w == 2 || w == 4 || w == 8 || w == 16) &&
            t.blocks_per_sm >= 0 && t.blocks_per_sm <= 32 && (kv == 0 || kv == 1 || kv == 2 || kv == 4) &&
-           (st == 0 || st == 64 || st == 128 || st == 256) && (t.use_pencils == 0 || t.use_pencils == 1);
+           (st == 0 || st == 64 || st == 128 || st == 256) && (t.use_pencils == 0 || t.use_pencils == 1) &&
+           (t.small_items == 0 || t.small_items == 1);
 }
 
 int decomp_slot(int K) { return K == 1 ? 0 : (K == 2 ? 1 : 2); }
@@ -186,7 +187,9 @@ void *host_mapped(const void *p) {
 // copy of the counters to pinned host memory.
 cudaError_t enqueue_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nullptr) {
     cudaError_t e;
-    if ((e = nf::launch_worklist(c, s, nf::pencils_active(c, c->tune, !dens && !f64)))) return e;
+    if ((e = nf::launch_worklist(c, s, nf::pencils_active(c, c->tune, !dens && !f64),
+                                 nf::small_active(c, c->tune, !dens && !f64))))
+        return e;
     if ((e = record_timing(c->ev_pair0, s))) return e;
     if ((e = nf::launch_pairs(c, acc, f64, c->tune, s, dens))) return e;
     if ((e = record_timing(c->ev_pair1, s))) return e;
@@ -259,7 +262,8 @@ int compute_forward(Ctx *c, void *acc, int f64, cudaStream_t s, float *dens = nu
                                      (uint64_t)c->tune.sinks_per_lane, (uint64_t)c->tune.warps_per_block,
                                      (uint64_t)c->tune.blocks_per_sm, (uint64_t)(uintptr_t)c->perm,
                                      (uint64_t)c->equal_mass, (uint64_t)(uintptr_t)dens,
-                                     (uint64_t)c->tune.source_tile, (uint64_t)c->tune.use_pencils};
+                                     (uint64_t)c->tune.source_tile, (uint64_t)c->tune.use_pencils,
+                                     (uint64_t)c->tune.small_items};
         e = run_graph(c, c->g_fwd, key,
                       [&](cudaStream_t cs) { return enqueue_forward(c, acc, f64, cs, dens); }, s);
     } else {
@@ -453,7 +457,7 @@ int init_impl(nf_ctx **out, int device, int n_boxes, const double *box_size, con
     memset(c->state_h, 0, sizeof(nf::DevState));
     // default launch shape: 4 sinks per lane, 4 warps per block (FP32);
     // the compensated variant keeps 2 sinks per lane to stay clear of spills
-    c->tune = nf_tuning{4, 4, 0, 1, 2, 0, 1};
+    c->tune = nf_tuning{4, 4, 0, 1, 2, 0, 1, 1};
     if (precision == NF_PREC_FP32_COMP || precision == NF_PREC_FP32_COMP_PAIR) c->tune.sinks_per_lane = 2;
     if (precision == NF_PREC_FP64_REF) c->tune.sinks_per_lane = 1, c->tune.vjp_sinks_per_lane = 1;
     *out = reinterpret_cast<nf_ctx *>(c);
@@ -825,6 +829,7 @@ int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
     out->max_occupancy = c->state_h->max_occ;
     out->n_items = c->state_h->n_items;
     out->n_pencils = c->state_h->n_pencils;
+    out->n_small = c->state_h->n_items - c->state_h->n_main;
     for (int a = 0; a < 3; ++a) out->momentum[a] = c->have_momentum ? c->mom_h[a] : 0.0;
     out->abs_momentum = c->have_momentum ? c->mom_h[3] : 0.0;
     float ms = 0.f;
@@ -845,7 +850,7 @@ int nf_get_stats(nf_ctx *ctx, nf_stats *out) {
 int nf_set_tuning(nf_ctx *ctx, const nf_tuning *t) {
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !t) return fail(c, NF_EINVAL, "nf_set_tuning: ctx and t are required");
-    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32], vjp_sinks_per_lane in {0,1,2,4}, source_tile in {0,64,128,256}, use_pencils in {0,1}");
+    if (!valid_tuning(*t)) return fail(c, NF_EINVAL, "nf_set_tuning: sinks_per_lane in {1,2,4}, warps_per_block in {2,4,8,16}, blocks_per_sm in [0,32], vjp_sinks_per_lane in {0,1,2,4}, source_tile in {0,64,128,256}, use_pencils in {0,1}, small_items in {0,1}");
     if (c->precision == NF_PREC_FP64_REF && (t->sinks_per_lane != 1 || t->vjp_sinks_per_lane > 1))
         return fail(c, NF_EINVAL, "nf_set_tuning: FP64 reference contexts use one sink per lane");
     c->tune = *t;
@@ -878,7 +883,8 @@ int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
             for (int st : ts) {
                 if (!tiles && st != 128) continue;
                 for (int pen = 0; pen < 2; ++pen) {
-                    nf_tuning t{k, w, 0, c->tune.use_graph, c->tune.vjp_sinks_per_lane, st, pen};
+                    nf_tuning t{k, w, 0, c->tune.use_graph, c->tune.vjp_sinks_per_lane, st, pen,
+                                c->tune.small_items};
                     if (pen && !nf::pencils_active(c, t, true)) continue;
                     cands.push_back(t);
                 }
@@ -897,13 +903,13 @@ int nf_autotune(nf_ctx *ctx, int reps, nf_tuning *best, void *stream) {
         c->tune = t;
         c->tune.use_graph = 0;
         if ((rc = ensure_decomp(c, t.sinks_per_lane, s))) break;
-        const bool pen = nf::pencils_active(c, t, true);
-        cudaError_t e = nf::launch_worklist(c, s, pen);
+        const bool pen = nf::pencils_active(c, t, true), sm = nf::small_active(c, t, true);
+        cudaError_t e = nf::launch_worklist(c, s, pen, sm);
         if (!e) e = nf::launch_pairs(c, acc, 0, c->tune, s);   // warm-up
         if (e) { rc = cuda_fail(c, e, "nf_autotune"); break; }
         float tot = 0.f;
         for (int r = 0; r < reps && !e; ++r) {
-            e = nf::launch_worklist(c, s, pen);
+            e = nf::launch_worklist(c, s, pen, sm);
             if (!e) e = cudaEventRecord(e0, s);
             if (!e) e = nf::launch_pairs(c, acc, 0, c->tune, s);
             if (!e) e = cudaEventRecord(e1, s);

@@ -25,6 +25,9 @@ constexpr int kPencilSinks = 64;
 constexpr int kColMax = 768;
 // Number of cost buckets of the work list (heaviest items are served first).
 constexpr int kBuckets = 64;
+// Items whose lanes split the sources at least 1 << kSmallLog2S ways (at most
+// 8 sinks with 4 sinks per lane) go to the small-item kernel when it is on.
+constexpr int kSmallLog2S = 4;
 // Max items one remainder of a cell can be cut into (see make_decomp()).
 constexpr int kDecompMax = 8;
 
@@ -107,8 +110,10 @@ struct DevState {
     unsigned long long interactions;
     int n_pencils;               // pencil items of the last work-list build
     int pencil_head;             // pencil kernel work counter
-    int bucket_count[kBuckets];
-    int bucket_cursor[kBuckets];
+    int n_main;                  // items [0, n_main) for the tiled kernels, the rest small items
+    int small_head;              // small-item kernel work counter
+    int bucket_count[2 * kBuckets];   // cost buckets; the upper half holds the small items
+    int bucket_cursor[2 * kBuckets];
 };
 
 // Decomposition of a cell's remainder of sinks into items: entry r lists
@@ -205,8 +210,9 @@ struct Ctx;
 // sort's gather reads the copy.
 cudaError_t launch_bin(Ctx *c, const float *pos, const float *mass, float m0, int64_t n,
                        cudaStream_t s, float *pos_copy = nullptr);
-cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils = false);
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils = false, bool small = false);
 bool pencils_active(const Ctx *c, const nf_tuning &t, bool density);
+bool small_active(const Ctx *c, const nf_tuning &t, bool plain_out);
 cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cudaStream_t s,
                          float *dens = nullptr);
 cudaError_t launch_vjp(Ctx *c, const float *w, float *grad, const nf_tuning &t, cudaStream_t s);

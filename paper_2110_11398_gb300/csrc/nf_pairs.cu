@@ -57,6 +57,12 @@ __device__ __forceinline__ int cost_bucket(int nsrc, int K, int log2s) {
     return __clzll(cost | 1ull);
 }
 
+// Bucket of an item with 2^log2s lanes per sink: small items (when the
+// small-item kernel is on) take the upper half, after every other item.
+__device__ __forceinline__ int item_bucket(int nsrc, int K, int log2s, int small_on) {
+    return cost_bucket(nsrc, K, log2s) + (small_on && log2s >= kSmallLog2S ? kBuckets : 0);
+}
+
 struct WLArgs {
     const BoxDev *boxes;
     int n_boxes;
@@ -70,6 +76,7 @@ struct WLArgs {
     DevState *st;
     WorkItem *items;
     int pencils_on;            // serve eligible pencils with k_pencils
+    int small_on;              // items of >= 2^kSmallLog2S lane splits go to k_pairs_small
     unsigned char *pencil_ok;  // [n_cells]: at a pencil's first cell, 1 if it is served as a pencil
     int *pencils;              // pencil items: first cell of each
 };
@@ -116,10 +123,10 @@ __global__ void __launch_bounds__(256) k_wl_pencils(WLArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
-    __shared__ int hist[kBuckets];
+    __shared__ int hist[2 * kBuckets];
     __shared__ unsigned long long s_inter;
     __shared__ int s_max;
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[b] = 0;
+    for (int b = threadIdx.x; b < 2 * kBuckets; b += blockDim.x) hist[b] = 0;
     if (threadIdx.x == 0) { s_inter = 0; s_max = 0; }
     __syncthreads();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,7 +149,7 @@ __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
                 if (q) atomicAdd(&hist[cost_bucket(ns, a.K, 0)], q);
                 for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
                     const int ent = a.decomp->entry[r][e];
-                    atomicAdd(&hist[cost_bucket(ns, a.K, ent & 0xff)], 1);
+                    atomicAdd(&hist[item_bucket(ns, a.K, ent & 0xff, a.small_on)], 1);
                 }
             }
         }
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
         if (mx) atomicMax(&s_max, mx);
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+    for (int b = threadIdx.x; b < 2 * kBuckets; b += blockDim.x)
         if (hist[b]) atomicAdd(&a.st->bucket_count[b], hist[b]);
     if (threadIdx.x == 0) {
         if (s_inter) atomicAdd(&a.st->interactions, s_inter);
@@ -166,10 +173,12 @@ __global__ void __launch_bounds__(256) k_wl_count(WLArgs a) {
 }
 
 __global__ void k_wl_scan(DevState *st) {
-    // one warp: exclusive scan of the bucket counts
+    // one warp: exclusive scan of the bucket counts; the small items' buckets
+    // (upper half) start at n_main
     const int lane = threadIdx.x;
     int run = 0;
-    for (int b0 = 0; b0 < kBuckets; b0 += 32) {
+    for (int b0 = 0; b0 < 2 * kBuckets; b0 += 32) {
+        if (b0 == kBuckets && lane == 0) st->n_main = run;
         const int v = st->bucket_count[b0 + lane];
         int inc = v;
         for (int o = 1; o < 32; o <<= 1) {
@@ -182,13 +191,14 @@ __global__ void k_wl_scan(DevState *st) {
     if (lane == 0) {
         st->n_items = run;
         st->queue_head = 0;
+        st->small_head = 0;
     }
 }
 
 __global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
-    __shared__ int cnt[kBuckets];
-    __shared__ int base[kBuckets];
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) cnt[b] = 0;
+    __shared__ int cnt[2 * kBuckets];
+    __shared__ int base[2 * kBuckets];
+    for (int b = threadIdx.x; b < 2 * kBuckets; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = 0, ns = 0, box = 0;
@@ -209,10 +219,10 @@ __global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
     if (n > 0) {
         if (q) atomicAdd(&cnt[cost_bucket(ns, a.K, 0)], q);
         for (int e = 0; e < a.decomp->n_entries[r]; ++e)
-            atomicAdd(&cnt[cost_bucket(ns, a.K, a.decomp->entry[r][e] & 0xff)], 1);
+            atomicAdd(&cnt[item_bucket(ns, a.K, a.decomp->entry[r][e] & 0xff, a.small_on)], 1);
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+    for (int b = threadIdx.x; b < 2 * kBuckets; b += blockDim.x) {
         base[b] = cnt[b] ? atomicAdd(&a.st->bucket_cursor[b], cnt[b]) : 0;
         cnt[b] = 0;
     }
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(256) k_wl_write(WLArgs a) {
         int off = first + q * full;
         for (int e = 0; e < a.decomp->n_entries[r]; ++e) {
             const int ent = a.decomp->entry[r][e];
-            const int b = cost_bucket(ns, a.K, ent & 0xff);
+            const int b = item_bucket(ns, a.K, ent & 0xff, a.small_on);
             const int p = base[b] + atomicAdd(&cnt[b], 1);
             WorkItem w;
             w.cell = (int)c;
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
     float *sx = sbase, *sy = sbase + TILE, *sz = sbase + 2 * TILE, *sm = sbase + 3 * TILE;
     int *pfx = reinterpret_cast<int *>(sbase + NF * TILE);
     int *dlt = pfx + a.tbl, *ofs = dlt + a.tbl;
-    const int n_items = a.st->n_items;
+    const int n_items = a.st->n_main;            // the small items, if split off, come after
 
     for (;;) {
         int it = 0;
@@ -552,6 +562,182 @@ __global__ void __launch_bounds__(512) k_pairs(PairArgs a) {
                     o[1] = v[1] * sc;
                     o[2] = v[2] * sc;
                 }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ small items
+// Per-warp pair table of an item's neighbourhood, for the small-item kernel:
+// ppf[ci] = exclusive prefix over the cells of their source pairs
+// ceil(n/2), sst[ci] = the cell's first sorted slot, scn[ci] = its source
+// count, sof[ci] = packed offset d + R. Returns the number of pairs.
+__device__ __forceinline__ int build_pair_table(const PairArgs &a, const BoxDev &B, int cell, int *ppf,
+                                                int *sst, int *scn, int *sof) {
+    const int lane = threadIdx.x & 31;
+    const int cpd = B.cpd, R = a.R, W = 2 * R + 1;
+    const int local = cell - B.cell_off;
+    const int cx = local / (cpd * cpd), cy = (local / cpd) % cpd, cz = local % cpd;
+    int run = 0;
+    for (int b0 = 0; b0 < a.nbr; b0 += 32) {
+        const int ci = b0 + lane;
+        int cnt = 0, st = 0, code = 0;
+        if (ci < a.nbr) {
+            const int ix = ci / (W * W), iy = (ci / W) % W, iz = ci % W;
+            const int gc = B.cell_off +
+                           (xwrap(B, cx + ix - R) * cpd + wrapc(cy + iy - R, cpd)) * cpd +
+                           wrapc(cz + iz - R, cpd);
+            st = a.cell_start[gc];
+            cnt = a.cell_start[gc + 1] - st;
+            code = ix | (iy << 8) | (iz << 16);
+        }
+        const int np = (cnt + 1) >> 1;
+        int inc = np;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (ci < a.nbr) {
+            ppf[ci] = run + inc - np;
+            sst[ci] = st;
+            scn[ci] = cnt;
+            sof[ci] = code;
+        }
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) ppf[a.nbr] = run;
+    __syncwarp();
+    return run;
+}
+
+// One source pair of a small item: pair P of the neighbourhood, shifted into
+// the sink cell's frame (an odd cell's last pair is padded with a source
+// that adds 0, as in the tiled kernel).
+struct SrcPair {
+    f2_t x, y, z, m;
+};
+
+template <bool EQ>
+__device__ __forceinline__ SrcPair load_pair(const PairArgs &a, const int *ppf, const int *sst,
+                                             const int *scn, const int *sof, int nbr, int P, int &ci) {
+    while (ci + 1 < nbr && ppf[ci + 1] <= P) ++ci;
+    const int j = 2 * (P - ppf[ci]);
+    const int st = sst[ci], cnt = scn[ci], code = sof[ci];
+    const float ox = (float)((code & 0xff) - a.R);
+    const float oy = (float)(((code >> 8) & 0xff) - a.R);
+    const float oz = (float)((code >> 16) - a.R);
+    const float4 p0 = a.sorted[st + j];
+    float4 p1 = make_float4(kFarAway, 0.f, 0.f, 0.f);
+    if (j + 1 < cnt) {
+        p1 = a.sorted[st + j + 1];
+        p1.x += ox;
+        p1.y += oy;
+        p1.z += oz;
+    }
+    SrcPair q;
+    q.x = f2_pack(p0.x + ox, p1.x);
+    q.y = f2_pack(p0.y + oy, p1.y);
+    q.z = f2_pack(p0.z + oz, p1.z);
+    q.m = EQ ? 0ull : f2_pack(p0.w, p1.w);
+    return q;
+}
+
+// Forward kernel for small items (plain FP32, Plummer, K = 4 sinks per lane):
+// the items of at most 8 sinks whose lanes split the sources 16 or 32 ways,
+// mostly the sinks of a cell left over after its full groups. They cost the
+// tiled kernel a whole neighbourhood of staging for a few sinks; here each
+// lane reads its own source pairs straight from the records (P = sp, sp + S,
+// ..., two pairs in flight), with no shared-memory tile and no warp
+// barrier. Same sink mapping, pair arithmetic and epilogue as k_pairs; the
+// lane sums are folded into the running totals every 8 pairs.
+template <bool EQ>
+__global__ void __launch_bounds__(128, 4) k_pairs_small(PairArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int K = 4;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *ppf = reinterpret_cast<int *>(smem_raw) + wib * 4 * a.tbl;
+    int *sst = ppf + a.tbl, *scn = sst + a.tbl, *sof = scn + a.tbl;
+    const int n_items = a.st->n_items, n_main = a.st->n_main;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = n_main + atomicAdd(&a.st->small_head, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        const int box = w.box_s >> 8, log2s = w.box_s & 0xff;
+        const int S = 1 << log2s, G = 32 >> log2s;
+        const int g = lane >> log2s, sp = lane & (S - 1);
+        const BoxDev *Bp = a.boxes + box;
+        const int npairs = build_pair_table(a, *Bp, w.cell, ppf, sst, scn, sof);
+        const f2_t eps2 = f2_pack(Bp->eps2, Bp->eps2);
+        f2_t xi[K], yi[K], zi[K], ax[K], ay[K], az[K], tx[K], ty[K], tz[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int si = g + G * k;
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (si < w.n) p = a.sorted[w.first + si];
+            xi[k] = f2_pack(p.x, p.x);
+            yi[k] = f2_pack(p.y, p.y);
+            zi[k] = f2_pack(p.z, p.z);
+            ax[k] = ay[k] = az[k] = tx[k] = ty[k] = tz[k] = 0ull;
+        }
+        const int n_it = (npairs - sp + S - 1) >> log2s;
+        int ci = 0;
+        for (int i = 0; i < n_it; i += 2) {
+            SrcPair q[2];
+            q[0] = load_pair<EQ>(a, ppf, sst, scn, sof, a.nbr, sp + (i << log2s), ci);
+            const bool two = i + 1 < n_it;
+            if (two) q[1] = load_pair<EQ>(a, ppf, sst, scn, sof, a.nbr, sp + ((i + 1) << log2s), ci);
+            else q[1] = SrcPair{f2_pack(kFarAway, kFarAway), 0ull, 0ull, 0ull};
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const f2_t dx = f2_sub(q[u].x, xi[k]);
+                    const f2_t dy = f2_sub(q[u].y, yi[k]);
+                    const f2_t dz = f2_sub(q[u].z, zi[k]);
+                    f2_t s2 = f2_fma(dx, dx, eps2);
+                    s2 = f2_fma(dy, dy, s2);
+                    s2 = f2_fma(dz, dz, s2);
+                    const f2_t r = f2_rsqrt(s2);
+                    f2_t f = f2_mul(f2_mul(r, r), r);
+                    if (!EQ) f = f2_mul(f, q[u].m);
+                    tx[k] = f2_fma(f, dx, tx[k]);
+                    ty[k] = f2_fma(f, dy, ty[k]);
+                    tz[k] = f2_fma(f, dz, tz[k]);
+                }
+            }
+            if ((i & 7) == 6 || i + 2 >= n_it) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    ax[k] = f2_add(ax[k], tx[k]);
+                    ay[k] = f2_add(ay[k], ty[k]);
+                    az[k] = f2_add(az[k], tz[k]);
+                    tx[k] = ty[k] = tz[k] = 0ull;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float v[3];
+            const f2_t hs[3] = {ax[k], ay[k], az[k]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float h0, h1;
+                f2_unpack(hs[c], h0, h1);
+                float sum = h0 + h1;
+                for (int o = 1; o < S; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                v[c] = sum;
+            }
+            const int si = g + G * k;
+            if (sp == 0 && si < w.n) {
+                const int i = a.perm[w.first + si];
+                const float sc = EQ ? __ldg(&Bp->gm) * __ldg(&Bp->inv_h2) : __ldg(&Bp->inv_h2);
+                float *o = reinterpret_cast<float *>(a.out) + 3 * (int64_t)i;
+                o[0] = v[0] * sc;
+                o[1] = v[1] * sc;
+                o[2] = v[2] * sc;
             }
         }
     }
@@ -1364,7 +1550,7 @@ void make_decomp(int K, Decomp *d) {
     }
 }
 
-cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils) {
+cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils, bool small) {
     cudaError_t e;
     // reset counters (everything but the error word)
     if ((e = cudaMemsetAsync(&c->state->n_items, 0, sizeof(DevState) - sizeof(int), s))) return e;
@@ -1381,6 +1567,7 @@ cudaError_t launch_worklist(Ctx *c, cudaStream_t s, bool pencils) {
     a.st = c->state;
     a.items = c->items;
     a.pencils_on = pencils ? 1 : 0;
+    a.small_on = small ? 1 : 0;
     a.pencil_ok = c->pencil_ok;
     a.pencils = c->pencils;
     const unsigned blocks = (unsigned)((c->n_sink_cells + 255) / 256 + (c->n_sink_cells == 0));
@@ -1407,6 +1594,20 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
     PairArgs args = make_args(c, acc, out_f64);
     args.dens = dens;
     cudaError_t e = launch_generic(c, fn, 0, args, t, s, tile);
+    if (!e && small_active(c, t, dens == nullptr && !out_f64)) {
+        // the small items, after the tiled ones
+        void *sf = c->equal_mass ? fptr(k_pairs_small<true>) : fptr(k_pairs_small<false>);
+        const size_t smem = sizeof(int) * 4 * (size_t)args.tbl * 4;
+        int per_sm = 0;
+        if (!e) e = prepare(sf, smem);
+        if (!e) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sf, 128, smem);
+        if (per_sm < 1) per_sm = 1;
+        void *sparams[] = {&args};
+        if (!e) {
+            c->launches += 1;
+            e = cudaLaunchKernel(sf, dim3(c->sm_count * per_sm), dim3(128), sparams, smem, s);
+        }
+    }
     if (e || !pencils_active(c, t, dens == nullptr && !out_f64)) return e;
     // the pencils, after the other items
     void *pf = c->equal_mass ? fptr(k_pencils<true>) : fptr(k_pencils<false>);
@@ -1421,6 +1622,11 @@ cudaError_t launch_pairs(Ctx *c, void *acc, int out_f64, const nf_tuning &t, cud
 
 // The pencil kernel serves the plain FP32 Plummer forward pass with FP32
 // output and no density, at K = 4 and R <= 2, when the tuning allows it.
+bool small_active(const Ctx *c, const nf_tuning &t, bool plain_out) {
+    return t.small_items && plain_out && c->precision == NF_PREC_FP32 && c->softening == NF_SOFT_PLUMMER &&
+           t.sinks_per_lane == 4;
+}
+
 bool pencils_active(const Ctx *c, const nf_tuning &t, bool plain_out) {
     return t.use_pencils && plain_out && c->precision == NF_PREC_FP32 &&
            c->softening == NF_SOFT_PLUMMER && c->R <= 2 && t.sinks_per_lane == 4;

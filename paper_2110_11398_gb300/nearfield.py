@@ -301,7 +301,8 @@ class NearField:
                 "max_occupancy": s.max_occupancy, "n_items": s.n_items,
                 "momentum": list(s.momentum), "abs_momentum": s.abs_momentum,
                 "bin_ms": s.bin_ms, "pair_ms": s.pair_ms, "kernel_launches": s.kernel_launches,
-                "far_ms": s.far_ms, "far_conv_ms": s.far_conv_ms, "n_pencils": s.n_pencils}
+                "far_ms": s.far_ms, "far_conv_ms": s.far_conv_ms, "n_pencils": s.n_pencils,
+                "n_small": s.n_small}
 
     @property
     def tuning(self) -> dict:
@@ -310,10 +311,11 @@ class NearField:
         return {"sinks_per_lane": t.sinks_per_lane, "warps_per_block": t.warps_per_block,
                 "blocks_per_sm": t.blocks_per_sm, "use_graph": t.use_graph,
                 "vjp_sinks_per_lane": t.vjp_sinks_per_lane, "source_tile": t.source_tile,
-                "use_pencils": t.use_pencils}
+                "use_pencils": t.use_pencils, "small_items": t.small_items}
 
     def set_tuning(self, sinks_per_lane=None, warps_per_block=None, blocks_per_sm=None,
-                   use_graph=None, vjp_sinks_per_lane=None, source_tile=None, use_pencils=None) -> None:
+                   use_graph=None, vjp_sinks_per_lane=None, source_tile=None, use_pencils=None,
+                   small_items=None) -> None:
         cur = self.tuning
         t = N.nf_tuning(cur["sinks_per_lane"] if sinks_per_lane is None else sinks_per_lane,
                         cur["warps_per_block"] if warps_per_block is None else warps_per_block,
@@ -321,7 +323,8 @@ class NearField:
                         cur["use_graph"] if use_graph is None else int(use_graph),
                         cur["vjp_sinks_per_lane"] if vjp_sinks_per_lane is None else vjp_sinks_per_lane,
                         cur["source_tile"] if source_tile is None else source_tile,
-                        cur["use_pencils"] if use_pencils is None else int(use_pencils))
+                        cur["use_pencils"] if use_pencils is None else int(use_pencils),
+                        cur["small_items"] if small_items is None else int(small_items))
         N.check(self._lib.nf_set_tuning(self._ctx, ctypes.byref(t)), self._ctx, "nf_set_tuning")
 
     def autotune(self, reps: int = 2, cache: str | None = None) -> dict:
@@ -337,7 +340,8 @@ class NearField:
             hit = load_tuning_cache(cache).get(key)
             if hit:
                 self.set_tuning(**{k: hit[k] for k in ("sinks_per_lane", "warps_per_block",
-                                                       "blocks_per_sm", "source_tile", "use_pencils")
+                                                       "blocks_per_sm", "source_tile", "use_pencils",
+                                                       "small_items")
                                 if k in hit})
                 return self.tuning
         t = N.nf_tuning()

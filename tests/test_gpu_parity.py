@@ -196,6 +196,32 @@ def test_pencils_on_and_off(dev, box_kind):
     assert_parity(gotm, refm, what=f"pencils, masses {box_kind}")
 
 
+@pytest.mark.parametrize("box_kind,pencils", [("lattice", 1), ("lattice", 0), ("clustered", 1)])
+def test_small_items_on_and_off(dev, box_kind, pencils):
+    """Work items of at most 8 sinks (the sinks a cell has left after its full
+    groups) served by the small-item kernel, which reads its sources straight
+    from the records, against the tiled kernel: both within the tolerance,
+    with equal and unequal masses, on the same items."""
+    if box_kind == "lattice":                   # ~64 per cell: many cells keep a few sinks over
+        box = synth.early(n_side=52, cpd=13)
+    else:
+        pos, _ = synth.clustered_box(48 ** 3, 9, n_halos=15)
+        box = synth.Box("cl48", pos, 1.0, 13, (1 / 48) / 40, 1 / 48 ** 3)
+    ref = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, m0=box.gm)
+    on, st_on = gpu_accel(box, dev, use_pencils=pencils, small_items=1)
+    off, st_off = gpu_accel(box, dev, use_pencils=pencils, small_items=0)
+    assert_parity(on, ref, what=f"small items {box_kind}")
+    assert_parity(off, ref, what=f"no small items {box_kind}")
+    assert st_on["n_small"] > 0 and st_off["n_small"] == 0
+    assert st_on["n_items"] == st_off["n_items"]
+    assert st_on["interactions"] == st_off["interactions"]
+    mass = np.random.default_rng(4).uniform(0.2, 3.0, box.n).astype(np.float32) / box.n
+    refm = oracle.accel(box.pos, box.L, box.cpd, box.R, box.eps, mass=mass.astype(np.float64))
+    gotm, stm = gpu_accel(box, dev, mass=mass, use_pencils=pencils, small_items=1)
+    assert stm["n_small"] > 0
+    assert_parity(gotm, refm, what=f"small items, masses {box_kind}")
+
+
 @pytest.mark.parametrize("tile,K,precision", [(64, 4, "fp32"), (256, 4, "fp32"), (64, 1, "fp32_comp"),
                                                (256, 2, "fp32_comp"), (256, 2, "fp32_comp_pair")])
 def test_source_tiles(dev, tile, K, precision):
