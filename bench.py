@@ -66,17 +66,17 @@ def dist_env():
 
 
 # DRAM bytes of one pair pass (dram__bytes_read.sum + dram__bytes_write.sum
-# of its k_pairs and k_pencils launches) from ncu captures, with the sha256
+# of its k_pairs, k_pairs_small and k_pencils launches) from ncu captures, with the sha256
 # of the kernel source they were taken on; a changed source reports null.
 # The late box's figure is the capture on the same recipe at 256^3 (CPD 65,
 # 2.094e12 interactions) scaled by the interactions (x 7.4453): a box too
 # large to capture counters on under the capture size rule.
-_PAIRS_SHA = "00d68ff7d586daed7405a7597cd22a0caf857fb5f8915c72e2d911e5200a5cae"
-_LATE256_PASS = 5.30775e9 + 0.24077e9 + 0.20642e9 + 0.04290e9
+_PAIRS_SHA = "02259944ce69327deb04a2a66d147b2d08985391539c492d93292116e08ca260"
+_LATE256_PASS = 2.53856e9 + 0.21453e9 + 2.44313e9 + 0.02202e9 + 0.20858e9 + 0.04282e9
 TRAFFIC_CAPTURES = {
-    ("early_256c_cpd65", "k_pairs+k_pencils"): (1.74694e9 + 0.01188e9 + 0.58422e9 + 0.21466e9, _PAIRS_SHA),
-    ("late_256c_cpd65", "k_pairs+k_pencils"): (_LATE256_PASS, _PAIRS_SHA),
-    ("late_512c_cpd129", "k_pairs+k_pencils"): (_LATE256_PASS * 15590655213356 / 2094020473656, _PAIRS_SHA),
+    ("early_256c_cpd65", "k_pairs+k_pairs_small+k_pencils"): (0.02521e9 + 0.00019e9 + 1.60836e9 + 0.00406e9 + 0.60734e9 + 0.21468e9, _PAIRS_SHA),
+    ("late_256c_cpd65", "k_pairs+k_pairs_small+k_pencils"): (_LATE256_PASS, _PAIRS_SHA),
+    ("late_512c_cpd129", "k_pairs+k_pairs_small+k_pencils"): (_LATE256_PASS * 15590655213356 / 2094020473656, _PAIRS_SHA),
 }
 
 
@@ -1092,7 +1092,7 @@ def run_ours(args):
     kernel = run.kernel + ("_f64" if fp64 else "") + ("_spline" if getattr(run, "law", "") == "spline" else "") \
         + ("_kde" if getattr(run, "kde_b", None) else "")
     if kernel == "k_pairs" and stats0.get("n_pencils", 0) > 0:
-        kernel = "k_pairs+k_pencils"      # the two launches of one pair pass, timed together
+        kernel = "k_pairs+k_pairs_small+k_pencils"   # the launches of one pair pass, timed together
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "traffic": (captured_traffic(run.name, kernel)
