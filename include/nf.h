@@ -111,9 +111,10 @@ typedef struct nf_stats {
  * block whose warps share the staged sources (the first 64 sinks of each
  * cell; where the neighbourhood is sparse enough), the rest as usual;
  * small_items = 1 lets the same pass (sinks_per_lane 4) serve the work items
- * of at most 8 sinks, mostly the sinks a cell has left after its full
- * groups, with a kernel whose lanes read their sources straight from the
- * records instead of staging tiles of the whole neighbourhood. */
+ * of at most 8 sinks over at most 32,768 sources, mostly the sinks a cell has
+ * left after its full groups, with a kernel whose lanes read their sources
+ * straight from the records instead of staging tiles of the whole
+ * neighbourhood. */
 typedef struct nf_tuning {
     int sinks_per_lane;
     int warps_per_block;

@@ -26,8 +26,12 @@ constexpr int kColMax = 768;
 // Number of cost buckets of the work list (heaviest items are served first).
 constexpr int kBuckets = 64;
 // Items whose lanes split the sources at least 1 << kSmallLog2S ways (at most
-// 8 sinks with 4 sinks per lane) go to the small-item kernel when it is on.
+// 8 sinks with 4 sinks per lane) over at most kSmallMaxSrc sources go to the
+// small-item kernel when it is on. Heavier ones (the last sinks of dense
+// cells) stay with the tiled kernel, whose cost order starts them early; run
+// after it, one of them would be a serial tail.
 constexpr int kSmallLog2S = 4;
+constexpr int kSmallMaxSrc = 32768;
 // Max items one remainder of a cell can be cut into (see make_decomp()).
 constexpr int kDecompMax = 8;
 

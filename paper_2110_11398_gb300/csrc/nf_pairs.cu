@@ -60,7 +60,8 @@ __device__ __forceinline__ int cost_bucket(int nsrc, int K, int log2s) {
 // Bucket of an item with 2^log2s lanes per sink: small items (when the
 // small-item kernel is on) take the upper half, after every other item.
 __device__ __forceinline__ int item_bucket(int nsrc, int K, int log2s, int small_on) {
-    return cost_bucket(nsrc, K, log2s) + (small_on && log2s >= kSmallLog2S ? kBuckets : 0);
+    const bool small = small_on && log2s >= kSmallLog2S && nsrc <= kSmallMaxSrc;
+    return cost_bucket(nsrc, K, log2s) + (small ? kBuckets : 0);
 }
 
 struct WLArgs {
@@ -645,7 +646,8 @@ __device__ __forceinline__ SrcPair load_pair(const PairArgs &a, const int *ppf, 
 
 // Forward kernel for small items (plain FP32, Plummer, K = 4 sinks per lane):
 // the items of at most 8 sinks whose lanes split the sources 16 or 32 ways,
-// mostly the sinks of a cell left over after its full groups. They cost the
+// over at most kSmallMaxSrc sources, mostly the sinks of a cell left over
+// after its full groups. They cost the
 // tiled kernel a whole neighbourhood of staging for a few sinks; here each
 // lane reads its own source pairs straight from the records (P = sp, sp + S,
 // ..., two pairs in flight), with no shared-memory tile and no warp
