@@ -71,10 +71,10 @@ def dist_env():
 # The late box's figure is the capture on the same recipe at 256^3 (CPD 65,
 # 2.094e12 interactions) scaled by the interactions (x 7.4453): a box too
 # large to capture counters on under the capture size rule.
-_PAIRS_SHA = "02259944ce69327deb04a2a66d147b2d08985391539c492d93292116e08ca260"
-_LATE256_PASS = 2.53856e9 + 0.21453e9 + 2.44313e9 + 0.02202e9 + 0.20858e9 + 0.04282e9
+_PAIRS_SHA = "4df3bf8fc06727b710122dc9226017be67f751b26c3b5e88c0c613f9080fce74"
+_LATE256_PASS = 2.79263e9 + 0.21597e9 + 1.61459e9 + 0.02114e9 + 0.20758e9 + 0.04288e9
 TRAFFIC_CAPTURES = {
-    ("early_256c_cpd65", "k_pairs+k_pairs_small+k_pencils"): (0.02521e9 + 0.00019e9 + 1.60836e9 + 0.00406e9 + 0.60734e9 + 0.21468e9, _PAIRS_SHA),
+    ("early_256c_cpd65", "k_pairs+k_pairs_small+k_pencils"): (0.02521e9 + 0.00019e9 + 1.52858e9 + 0.00405e9 + 0.59883e9 + 0.21481e9, _PAIRS_SHA),
     ("late_256c_cpd65", "k_pairs+k_pairs_small+k_pencils"): (_LATE256_PASS, _PAIRS_SHA),
     ("late_512c_cpd129", "k_pairs+k_pairs_small+k_pencils"): (_LATE256_PASS * 15590655213356 / 2094020473656, _PAIRS_SHA),
 }
