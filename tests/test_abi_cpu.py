@@ -118,3 +118,27 @@ def test_missing_library_fails_loudly(tmp_path):
             N.load(str(tmp_path / "nope.so"))
         finally:
             N._lib = N._lib_saved
+
+
+@pytest.mark.parametrize("name", ["nf_stats", "nf_tuning"])
+def test_binding_structs_match_the_header(name, tmp_path):
+    """The ctypes structures of the binding have the header's size and field
+    offsets (a C program compiled against include/nf.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    st = getattr(N, name)
+    fields = [f[0] for f in st._fields_]
+    prog = ['#include <stddef.h>', '#include <stdio.h>', '#include "nf.h"', "int main(void) {",
+            f'  printf("%zu\\n", sizeof({name}));']
+    prog += [f'  printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [ctypes.sizeof(st)] + [getattr(st, f).offset for f in fields]
+    assert got == want, (name, got, want)
