@@ -412,6 +412,26 @@ def test_host_buffer_path_pinned_ragged_and_unaligned(dev):
     assert np.array_equal(hacc, a_dev)
 
 
+@pytest.mark.parametrize("pin_pos,pin_acc", [(True, False), (False, True)])
+def test_host_buffer_path_mixed_buffers(dev, pin_pos, pin_acc):
+    """One page-locked buffer and one pageable one: the kernels read the
+    page-locked positions (or write the page-locked accelerations) directly,
+    the other side goes through the staged copy; the result equals the
+    device path's bit for bit."""
+    box = synth.tiny(seed=4)
+    hpos = torch.from_numpy(box.pos).pin_memory().numpy() if pin_pos else box.pos.copy()
+    if pin_acc:
+        hacc = torch.full((box.n, 3), float("nan"), dtype=torch.float32).pin_memory().numpy()
+    else:
+        hacc = np.full((box.n, 3), np.nan, np.float32)
+    nf = make_nf(box, dev)
+    nf.accel_host(hpos, gm=box.gm, out=hacc)
+    nf.bin(torch.from_numpy(box.pos).to(dev), gm=box.gm)
+    a_dev = nf.accel().cpu().numpy()
+    nf.close()
+    assert np.array_equal(hacc, a_dev)
+
+
 def test_host_buffer_path_matches_device_path(dev):
     box = synth.tiny(seed=3)
     nf = make_nf(box, dev)
